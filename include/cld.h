@@ -1,0 +1,180 @@
+/*
+ * cld.h -- C ABI of libcld, a single-GPU (sm_103a) implementation of the
+ * stochastic Chebyshev log-determinant estimator of Han, Malioutov and Shin,
+ * "Large-scale Log-determinant Computation through Stochastic Chebyshev
+ * Expansions" (arXiv 1503.06394).
+ *
+ * What is computed (Algorithm 1, restated on a general spectral interval):
+ *   given a symmetric positive definite B with spectrum in [a, b], the shifted
+ *   matrix At = (2B - (a+b) I) / (b - a) has spectrum in [-1, 1] (the affine
+ *   map of Sec. 4.1).  With M Rademacher probes v_p (Sec. 2.2), the
+ *   three-term recurrence w_0 = v, w_1 = At v, w_{j+1} = 2 At w_j - w_{j-1}
+ *   (Sec. 2.2, Eq. chebreq) yields moments t_{j,p} = v_p^T w_j, and
+ *     logdet B ~= Gamma = (1/M) sum_p sum_{j=0..n} c_j t_{j,p},
+ *   where c_j are the degree-n Chebyshev interpolation coefficients of log on
+ *   [a, b] at the first-kind nodes (Sec. 2.1).  For a general non-singular C
+ *   (Algorithm 2, Sec. 3.2) the same runs on C^T C, applied as C then C^T, and
+ *   the result is halved: log|det C| = 1/2 logdet(C^T C).
+ *
+ * Conventions
+ *   - Every call returns a cld_status; no C++ exception crosses the ABI.
+ *     cld_last_error() returns a thread-local message for the last failure.
+ *   - Matrix arrays are BORROWED device pointers: the caller keeps them alive
+ *     and unchanged until cld_destroy.  CSR rows need not be sorted; repeated
+ *     (row, col) entries are added.
+ *   - All device scratch memory comes from a caller-supplied workspace
+ *     (cld_workspace_size / cld_set_workspace).  The library allocates no
+ *     device memory of its own except where an entry point says so.
+ *   - Work is enqueued on the stream given at creation.  cld_estimate
+ *     synchronises that stream once to return host doubles.
+ *   - Probe vectors are never stored: entry v[i,p] in {+1,-1} is regenerated
+ *     from Philox4x32-10 (Salmon et al., SC'11) with key = seed (low word,
+ *     high word) and counter = (i low word, i high word, p / 128, 0):
+ *     v = 1 - 2 * bit (p mod 32) of output word ((p / 32) mod 4).
+ *   - Recurrence vectors are FP32; stored matrix values are FP32, BF16 or
+ *     FP64; coefficients, moments and the final reduction are FP64.
+ */
+#ifndef CLD_H
+#define CLD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define CLD_API __attribute__((visibility("default")))
+#else
+#define CLD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cld_ctx* cld_handle;
+
+typedef enum {
+    CLD_OK = 0,
+    CLD_ERR_INVALID = 1,     /* bad argument, malformed CSR, NULL pointer       */
+    CLD_ERR_INTERVAL = 2,    /* a <= 0, a >= b, or interval not set / not finite */
+    CLD_ERR_SPECTRUM = 3,    /* some |t_{j,p}| > d (1 + 1e-3) or not finite:    */
+                             /* the spectrum is not inside [a, b]                */
+    CLD_ERR_NOMEM = 4,       /* workspace missing or smaller than required      */
+    CLD_ERR_CUDA = 5,        /* a CUDA runtime call failed                      */
+    CLD_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                   */
+    CLD_ERR_UNSUPPORTED = 7  /* valid request this build does not implement     */
+} cld_status;
+
+typedef enum { CLD_F32 = 0, CLD_BF16 = 1, CLD_F64 = 2 } cld_dtype;
+
+/* CLD_SPD: the matrix B itself is symmetric positive definite (Algorithm 1).
+ * CLD_GENERAL: the matrix C is a general non-singular matrix; the estimate is
+ * of log|det C| = 1/2 logdet(C^T C) and the interval bounds the spectrum of
+ * C^T C, i.e. [sigma_min^2, sigma_max^2] (Algorithm 2). */
+typedef enum { CLD_SPD = 0, CLD_GENERAL = 1 } cld_kind;
+
+/* Largest probe count handled by one pass; larger M runs in panels of 128. */
+#define CLD_PROBE_PANEL 128
+
+/* Creates a handle for a d x d CSR matrix on the device.
+ *   rowptr: d+1 int64 (device), rowptr[0] = 0, non-decreasing, rowptr[d] = nnz
+ *   col:    nnz int32 (device), 0 <= col < d
+ *   val:    nnz values (device) of type val_dtype
+ *   stream: cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Only host-side checks run here (sizes, NULLs, d < 2^31); the arrays are
+ * checked on the device by cld_set_workspace.  Errors: CLD_ERR_INVALID. */
+CLD_API cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t* rowptr,
+                          const int32_t* col, const void* val, cld_dtype val_dtype,
+                          cld_kind kind, void* stream);
+
+/* Bytes of device workspace an estimate of degree n with M probes needs
+ * (with_grad != 0: also enough for cld_grad).  Errors: CLD_ERR_INVALID. */
+CLD_API cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes);
+
+/* Attaches caller-owned device workspace (at least 256-byte aligned) and
+ * validates the CSR arrays on the device (monotone rowptr, column range,
+ * finite values).  The workspace must stay alive until cld_destroy or the
+ * next cld_set_workspace.  Errors: CLD_ERR_INVALID (malformed CSR or
+ * unaligned pointer), CLD_ERR_CUDA. */
+CLD_API cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes);
+
+/* Sets the spectral interval [a, b] that must contain the spectrum of B
+ * (CLD_SPD) or of C^T C (CLD_GENERAL), Sec. 3 ("loose lower and upper bounds
+ * suffice").  Errors: CLD_ERR_INTERVAL if !(0 < a < b) or not finite. */
+CLD_API cld_status cld_set_interval(cld_handle h, double a, double b);
+
+/* Computes an interval on the device and stores it on the handle (Sec. 3.2).
+ * CLD_SPD: a = min_i (B_ii - R_i), b = max_i (B_ii + R_i) (Gershgorin,
+ * R_i = sum_{k != i} |B_ik|); a must come out positive, else
+ * CLD_ERR_INTERVAL.  If lanczos_iters > 0, b is tightened to
+ * min(b, theta_max + r), theta_max the largest Ritz value of a Lanczos run of
+ * that many steps from a Philox start vector and r its residual norm; a is
+ * never taken from Lanczos.
+ * CLD_GENERAL: b = ||C||_1 ||C||_inf (the square of the paper's sigma_max
+ * bound); a = alpha * beta with alpha = min_i (|C_ii| - R_i) and
+ * beta = min_i (|C_ii| - S_i) (R_i, S_i the off-diagonal absolute row and
+ * column sums) when both are positive: Varah's bounds ||C^-1||_inf <= 1/alpha
+ * and ||C^-1||_1 <= 1/beta give sigma_min^2 >= alpha beta, the diagonal-
+ * dominance route of Sec. 3.2.  Otherwise CLD_ERR_INTERVAL.
+ * Either pointer may be NULL.  Needs the workspace.  Errors:
+ * CLD_ERR_INTERVAL, CLD_ERR_NOMEM, CLD_ERR_CUDA. */
+CLD_API cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a, double* b);
+
+/* Runs the estimator: degree n >= 0, M >= 1 probes, probe seed `seed`.
+ *   logdet_out: Gamma (CLD_SPD: logdet B; CLD_GENERAL: log|det C|)
+ *   stderr_out: std over probes of Gamma_p divided by sqrt(M) (NULL ok;
+ *               NaN when M = 1); for CLD_GENERAL it is halved as well
+ *   moments_out: NULL or host array of (n+1) x M doubles, t[j*M + p]
+ * Needs an interval and a workspace of cld_workspace_size(h, n, M, 0).
+ * Errors: CLD_ERR_INVALID (n < 0, M < 1), CLD_ERR_INTERVAL, CLD_ERR_NOMEM,
+ * CLD_ERR_SPECTRUM (outputs are still written), CLD_ERR_CUDA. */
+CLD_API cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
+                        double* stderr_out, double* moments_out);
+
+/* After a successful cld_estimate: copies the n+1 coefficients c_j used and
+ * the M per-probe estimates Gamma_p to host arrays (either may be NULL). */
+CLD_API cld_status cld_last_details(cld_handle h, double* coeffs_out, double* gamma_p_out);
+
+/* Gradient of the estimate (same n, M, seed and interval, interval held fixed)
+ * with respect to every stored value: dvalues_dev[k] = dGamma / d val[k], an
+ * FP32 device array of nnz entries, each stored entry treated as an
+ * independent variable.  Reverse-mode differentiation of the recurrence of
+ * Sec. 2.2 (an extension; the paper has no gradient).  CLD_SPD only.
+ * Needs cld_workspace_size(h, n, M, 1).  Errors as cld_estimate, plus
+ * CLD_ERR_UNSUPPORTED for CLD_GENERAL. */
+CLD_API cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
+                    float* dvalues_dev);
+
+/* One-shot estimate from HOST arrays: copies the CSR (rowptr, col, val as
+ * above but in host memory, ideally pinned) into the front of the device
+ * workspace, runs cld_estimate on [a, b] and returns Gamma and its stderr.
+ * Workspace size: cld_host_workspace_size.  Nothing is kept after return.
+ * Errors: as cld_create_csr, cld_set_workspace and cld_estimate. */
+CLD_API cld_status cld_host_workspace_size(int64_t d, int64_t nnz, cld_dtype val_dtype, int n, int M,
+                                   size_t* bytes);
+CLD_API cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* rowptr_host,
+                               const int32_t* col_host, const void* val_host, cld_dtype val_dtype,
+                               cld_kind kind, double a, double b, int n, int M, uint64_t seed,
+                               void* workspace_dev, size_t workspace_bytes, void* stream,
+                               double* logdet_out, double* stderr_out);
+
+/* Timing of the dominant kernel.  When on, every cld_estimate records CUDA
+ * events on its stream around the general recurrence steps (j >= 2) and
+ * cld_last_timing returns their elapsed time and the number of such launches
+ * in the last estimate.  Off by default. */
+CLD_API cld_status cld_set_profiling(cld_handle h, int on);
+CLD_API cld_status cld_last_timing(cld_handle h, float* step_ms, int* step_launches, int* total_launches);
+
+/* Kernel configuration of the recurrence step, for reports: probe panel width
+ * (padded M), lanes per row, CTAs per launch, threads per CTA. */
+CLD_API cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row, int* ctas,
+                             int* threads);
+
+CLD_API void cld_destroy(cld_handle h);
+CLD_API const char* cld_last_error(void);
+CLD_API const char* cld_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLD_H */

@@ -82,6 +82,8 @@ def _load():
             lib.oracle_gershgorin.restype = None
             lib.oracle_sigma_max_bound.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p]
             lib.oracle_sigma_max_bound.restype = ctypes.c_double
+            lib.oracle_dominance_margins.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, _f64p, _f64p]
+            lib.oracle_dominance_margins.restype = None
             lib.oracle_logdet_cholesky.argtypes = [ctypes.c_int64, _f64p, _f64p]
             lib.oracle_logdet_cholesky.restype = ctypes.c_int
             lib.oracle_grad.argtypes = [ctypes.c_int64, _i64p, _i32p, _f64p, ctypes.c_double,
@@ -241,6 +243,15 @@ def sigma_max_bound(rowptr, col, val) -> float:
     """sqrt(||C||_1 ||C||_inf) >= sigma_max(C) (Sec. 3.2)."""
     d, rowptr, col, val = _csr(rowptr, col, val)
     return float(_load().oracle_sigma_max_bound(d, _p(rowptr, _i64p), _p(col, _i32p), _p(val, _f64p)))
+
+
+def dominance_margins(rowptr, col, val):
+    """(alpha, beta): row and column diagonal-dominance margins of a general C."""
+    d, rowptr, col, val = _csr(rowptr, col, val)
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _load().oracle_dominance_margins(d, _p(rowptr, _i64p), _p(col, _i32p), _p(val, _f64p),
+                                     ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
 
 
 # ----------------------------------------------------------------------------- exact

@@ -394,6 +394,40 @@ EXPORT double oracle_sigma_max_bound(int64_t d, const int64_t* rowptr, const int
     return sqrt(norm_1 * norm_inf);
 }
 
+/* Diagonal-dominance margins of a general C (Sec. 3.2: sigma_min is easy for
+ * diagonally dominant matrices).  alpha = min_i (|C_ii| - R_i) over rows,
+ * beta = min_i (|C_ii| - S_i) over columns (R_i, S_i: off-diagonal absolute
+ * row / column sums).  Varah's bounds ||C^-1||_inf <= 1/alpha and
+ * ||C^-1||_1 <= 1/beta give sigma_min(C)^2 >= alpha * beta when both are > 0. */
+EXPORT void oracle_dominance_margins(int64_t d, const int64_t* rowptr, const int32_t* col,
+                                     const double* val, double* alpha, double* beta) {
+    double* diag = (double*)calloc((size_t)(d > 0 ? d : 1), sizeof(double));
+    double* colsum = (double*)calloc((size_t)(d > 0 ? d : 1), sizeof(double));
+    if (!diag || !colsum) { free(diag); free(colsum); *alpha = *beta = NAN; return; }
+    double amin = INFINITY;
+    for (int64_t i = 0; i < d; ++i) {
+        double r = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            if (col[k] == i) diag[i] += val[k];
+            else { r += fabs(val[k]); colsum[col[k]] += fabs(val[k]); }
+        }
+        (void)r;
+    }
+    for (int64_t i = 0; i < d; ++i) {
+        double r = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k)
+            if (col[k] != i) r += fabs(val[k]);
+        if (fabs(diag[i]) - r < amin) amin = fabs(diag[i]) - r;
+    }
+    double bmin = INFINITY;
+    for (int64_t i = 0; i < d; ++i)
+        if (fabs(diag[i]) - colsum[i] < bmin) bmin = fabs(diag[i]) - colsum[i];
+    *alpha = amin;
+    *beta = bmin;
+    free(diag);
+    free(colsum);
+}
+
 /* ------------------------------------------------------------------------- */
 /* Exact reference: dense Cholesky B = L L^T, log det B = 2 sum_i log L_ii     */
 /* (Sec. 1).  A is d x d row-major and is overwritten by L in its lower part. */

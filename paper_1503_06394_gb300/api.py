@@ -1,0 +1,142 @@
+"""Convenience layer over the C ABI: keeps the CSR arrays and the workspace as
+torch CUDA tensors and forwards to libcld.  No arithmetic of the estimator is
+done here."""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+_DTYPES = {"f32": B.CLD_F32, "bf16": B.CLD_BF16, "f64": B.CLD_F64}
+_KINDS = {"spd": B.CLD_SPD, "general": B.CLD_GENERAL}
+
+
+def _torch():
+    import torch
+
+    if not torch.cuda.is_available():
+        raise RuntimeError("a CUDA device is required (libcld has no CPU path)")
+    return torch
+
+
+def _values_tensor(torch, val, dtype, device):
+    if isinstance(val, np.ndarray):
+        if dtype == "bf16":
+            if val.dtype != np.uint16:
+                raise TypeError("bf16 values must be given as uint16 bit patterns or a torch.bfloat16 tensor")
+            return torch.from_numpy(val.view(np.int16)).to(device).view(torch.bfloat16)
+        return torch.from_numpy(np.ascontiguousarray(val, dtype=np.float32 if dtype == "f32" else np.float64)).to(device)
+    want = {"f32": torch.float32, "bf16": torch.bfloat16, "f64": torch.float64}[dtype]
+    if val.dtype != want:
+        raise TypeError("values tensor must be %s for dtype %s" % (want, dtype))
+    return val.to(device).contiguous()
+
+
+class CsrLogdet:
+    """A CSR matrix on the GPU bound to a libcld handle.
+
+    rowptr (d+1, int64), col (nnz, int32), val (nnz; f32 / bf16 / f64) may be
+    numpy arrays or torch tensors; they are copied to ``device`` once and kept
+    alive for the handle's lifetime.  ``kind='general'`` estimates log|det C|
+    through C^T C (Algorithm 2)."""
+
+    def __init__(self, rowptr, col, val, dtype: str = "f32", kind: str = "spd", device="cuda", stream=None):
+        torch = _torch()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.rowptr = torch.as_tensor(np.asarray(rowptr, dtype=np.int64) if isinstance(rowptr, np.ndarray) else rowptr,
+                                      dtype=torch.int64).to(self.device).contiguous()
+        self.col = torch.as_tensor(np.asarray(col, dtype=np.int32) if isinstance(col, np.ndarray) else col,
+                                   dtype=torch.int32).to(self.device).contiguous()
+        self.val = _values_tensor(torch, val, dtype, self.device)
+        self.d = int(self.rowptr.numel() - 1)
+        self.nnz = int(self.col.numel())
+        self.dtype = dtype
+        self.kind = kind
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = B.cld_create_csr(self.d, self.nnz, self.rowptr, self.col, self.val, _DTYPES[dtype],
+                                  _KINDS[kind], self.stream.cuda_stream)
+        self.ws = None
+        self.ws_bytes = 0
+
+    # -- workspace ---------------------------------------------------------
+    def reserve(self, n: int, M: int, with_grad: int = 0):
+        need = B.cld_workspace_size(self.h, n, M, with_grad)
+        if self.ws is None or self.ws_bytes < need:
+            self.ws = None
+            self.ws = self.torch.empty(need, dtype=self.torch.uint8, device=self.device)
+            self.ws_bytes = need
+            B.cld_set_workspace(self.h, self.ws, need)
+        return need
+
+    # -- interval ----------------------------------------------------------
+    def set_interval(self, a: float, b: float):
+        B.cld_set_interval(self.h, float(a), float(b))
+
+    def auto_interval(self, lanczos_iters: int = 0):
+        self.reserve(0, 1)
+        return B.cld_auto_interval(self.h, lanczos_iters)
+
+    # -- estimate ----------------------------------------------------------
+    def estimate(self, n: int, M: int, seed: int = 0, moments: bool = False, details: bool = False,
+                 raise_on_spectrum: bool = True):
+        self.reserve(n, M)
+        g, se, t, st = B.cld_estimate(self.h, n, M, seed, moments=moments, raise_on_spectrum=raise_on_spectrum)
+        out = {"logdet": g, "stderr": se, "status": st}
+        if moments:
+            out["t"] = t
+        if details and st == B.CLD_OK:
+            out["c"], out["gamma_p"] = B.cld_last_details(self.h, n, M)
+        return out
+
+    def set_profiling(self, on: bool = True):
+        B.cld_set_profiling(self.h, on)
+
+    def last_timing(self):
+        return B.cld_last_timing(self.h)
+
+    def launch_config(self, M: int):
+        return B.cld_launch_config(self.h, M)
+
+    def close(self):
+        if getattr(self, "h", None):
+            B.cld_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def logdet(rowptr, col, val, n: int, M: int, seed: int = 0, interval=None, dtype: str = "f32",
+           kind: str = "spd", lanczos_iters: int = 0):
+    """One-call estimate: returns (logdet, stderr).  ``interval=None`` computes
+    [a, b] on the device (Gershgorin / norm bounds, optional Lanczos)."""
+    m = CsrLogdet(rowptr, col, val, dtype=dtype, kind=kind)
+    try:
+        if interval is None:
+            m.auto_interval(lanczos_iters)
+        else:
+            m.set_interval(*interval)
+        r = m.estimate(n, M, seed)
+        return r["logdet"], r["stderr"]
+    finally:
+        m.close()
+
+
+def logdet_host(rowptr, col, val, a: float, b: float, n: int, M: int, seed: int = 0, dtype: str = "f32",
+                kind: str = "spd", workspace=None, stream=None):
+    """Estimate from host arrays through ``cld_logdet_csr_host`` (the library
+    copies them to the device itself).  ``workspace``: optional preallocated
+    uint8 CUDA tensor of at least ``cld_host_workspace_size`` bytes."""
+    torch = _torch()
+    d = int(len(rowptr) - 1)
+    nnz = int(len(col))
+    need = B.cld_host_workspace_size(d, nnz, _DTYPES[dtype], n, M)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return B.cld_logdet_csr_host(d, nnz, rowptr, col, val, _DTYPES[dtype], _KINDS[kind], float(a), float(b),
+                                 n, M, seed, workspace, need, s.cuda_stream)

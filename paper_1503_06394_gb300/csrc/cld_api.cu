@@ -1,0 +1,509 @@
+// C ABI of libcld (declared in include/cld.h): handle management, workspace
+// layout, and the driver that enqueues one estimate of the Chebyshev-Hutchinson
+// log-determinant (Algorithm 1; Algorithm 2 for general C) on a CUDA stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/cld.h"
+#include "cld_internal.cuh"
+
+namespace cld {
+cudaError_t launch_set_seed(Params* prm, uint64_t seed, cudaStream_t s);
+cudaError_t launch_transpose(int64_t d, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                             const void* val, int vsize, int64_t* rowptrT, int32_t* colT, void* valT,
+                             int64_t* scratch, int grid, cudaStream_t s);
+cudaError_t launch_general_bounds(int64_t d, const int64_t* rowptr, const int32_t* col,
+                                  const void* val, const int64_t* rowptrT, const int32_t* colT,
+                                  const void* valT, int dtype, double* partial, int grid,
+                                  Params* prm, uint32_t* flags, cudaStream_t s);
+cudaError_t launch_lanczos(int64_t d, const int64_t* rowptr, const int32_t* col, const void* val,
+                           int dtype, int iters, double* vecs, double* scal, int grid,
+                           Params* prm, uint32_t* flags, cudaStream_t s);
+}  // namespace cld
+
+using namespace cld;
+
+// ---------------------------------------------------------------- errors
+static thread_local std::string g_err;
+
+static cld_status fail(cld_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                     \
+    do {                                                                                   \
+        cudaError_t e_ = (expr);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(CLD_ERR_CUDA, "%s failed: %s", #expr, cudaGetErrorString(e_));   \
+    } while (0)
+
+static inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+static int value_size(cld_dtype t) { return t == CLD_F32 ? 4 : t == CLD_BF16 ? 2 : 8; }
+
+// ---------------------------------------------------------------- handle
+struct cld_ctx {
+    int64_t d = 0, nnz = 0;
+    const int64_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const void* val = nullptr;
+    cld_dtype dtype = CLD_F32;
+    cld_kind kind = CLD_SPD;
+    cudaStream_t stream = nullptr;
+    int device = 0, sms = 1;
+
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ready = false;  // workspace attached and CSR validated (and transposed)
+
+    double a = 0.0, b = 0.0;
+    bool have_interval = false;
+
+    int last_n = -1, last_M = -1;
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    float last_step_ms = 0.f;
+    int last_step_launches = 0, last_total_launches = 0;
+};
+
+// Workspace layout.  Front: fixed header (parameters, result, flags), then
+// (general C only) the transposed CSR of C, then the per-run region.
+struct Layout {
+    size_t params, result, flags, rowptrT, colT, valT, tscratch, run;  // fixed part
+    size_t coeffs, coef_scratch, T, gamma_p, tpart, gpart, vbits, W[3], Y, lanczos, total;
+    int panel, nw, grid, ggrid;
+};
+
+static int panel_for(int M) {
+    if (M >= kMaxPanel) return kMaxPanel;
+    int p = 4;
+    while (p < M) p <<= 1;
+    return p;
+}
+
+static int step_grid(const cld_ctx* h, int panel) {
+    const int rows_per_cta = (kThreads / 32) * (128 / panel);
+    const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
+    const int64_t full = (int64_t)step_ctas_per_sm(panel, (int)h->dtype) * h->sms;
+    int64_t g = need < full ? need : full;
+    return (int)(g > 0 ? g : 1);
+}
+
+static int stream_grid(const cld_ctx* h) {
+    const int64_t need = (h->d + kThreads - 1) / kThreads;
+    const int64_t full = (int64_t)h->sms * 8;
+    int64_t g = need < full ? need : full;
+    return (int)(g > 0 ? g : 1);
+}
+
+static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
+    Layout L{};
+    size_t o = 0;
+    L.params = o; o += align_up(sizeof(Params));
+    L.result = o; o += align_up(sizeof(Result));
+    L.flags = o; o += 256;
+    if (h->kind == CLD_GENERAL) {
+        L.rowptrT = o; o += align_up((size_t)(h->d + 1) * 8);
+        L.colT = o; o += align_up((size_t)h->nnz * 4);
+        L.valT = o; o += align_up((size_t)h->nnz * value_size(h->dtype));
+        L.tscratch = o; o += align_up((size_t)(h->d + 1) * 8);
+    }
+    L.run = o;
+    const int nn = n > 0 ? n : 0;
+    const int MM = M > 0 ? M : 1;
+    L.panel = panel_for(MM);
+    L.nw = sign_words(L.panel);
+    L.grid = step_grid(h, L.panel);
+    L.ggrid = stream_grid(h);
+    L.coeffs = o; o += align_up((size_t)(nn + 1) * 8);
+    L.coef_scratch = o; o += align_up((size_t)5 * (nn + 1) * 8);
+    L.T = o; o += align_up((size_t)(nn + 1) * MM * 8);
+    L.gamma_p = o; o += align_up((size_t)MM * 8);
+    L.tpart = o; o += align_up((size_t)(nn > 0 ? nn : 1) * L.grid * L.panel * 8);
+    L.gpart = o; o += align_up((size_t)4 * L.ggrid * 8 + 64);  // 4 doubles per CTA (general bounds)
+    L.vbits = o; o += align_up((size_t)h->d * L.nw * 4);
+    const size_t wb = align_up((size_t)h->d * L.panel * 4);
+    for (int i = 0; i < 3; ++i) { L.W[i] = o; o += wb; }
+    if (h->kind == CLD_GENERAL) { L.Y = o; o += wb; }
+    // Lanczos scratch (5 FP64 vectors + scalars) reuses the W buffers when they are
+    // large enough, else gets its own region.
+    const size_t lz = align_up((size_t)5 * h->d * 8) + align_up((size_t)(8000 + L.ggrid + 64) * 8);
+    if (lz > 3 * wb) { L.lanczos = o; o += lz; } else { L.lanczos = L.W[0]; }
+    (void)with_grad;
+    L.total = o;
+    return L;
+}
+
+template <typename T>
+static T* at(cld_ctx* h, size_t off) { return reinterpret_cast<T*>(h->ws + off); }
+
+static cld_status check_handle(cld_handle h) {
+    if (!h) return fail(CLD_ERR_INVALID, "NULL handle");
+    return CLD_OK;
+}
+
+extern "C" {
+
+const char* cld_last_error(void) { return g_err.c_str(); }
+const char* cld_version(void) { return "libcld 0.1 (sm_103a)"; }
+
+cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t* rowptr,
+                          const int32_t* col, const void* val, cld_dtype val_dtype,
+                          cld_kind kind, void* stream) {
+    if (!out) return fail(CLD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (d < 0 || nnz < 0) return fail(CLD_ERR_INVALID, "negative size (d=%lld, nnz=%lld)",
+                                      (long long)d, (long long)nnz);
+    if (d >= (int64_t)INT32_MAX) return fail(CLD_ERR_INVALID, "d must be < 2^31 (int32 columns)");
+    if (!rowptr || (nnz > 0 && (!col || !val)))
+        return fail(CLD_ERR_INVALID, "NULL CSR array");
+    if (val_dtype != CLD_F32 && val_dtype != CLD_BF16 && val_dtype != CLD_F64)
+        return fail(CLD_ERR_INVALID, "unknown value dtype %d", (int)val_dtype);
+    if (kind != CLD_SPD && kind != CLD_GENERAL) return fail(CLD_ERR_INVALID, "unknown kind %d", (int)kind);
+    cld_ctx* h = new (std::nothrow) cld_ctx;
+    if (!h) return fail(CLD_ERR_NOMEM, "host allocation failed");
+    h->d = d; h->nnz = nnz; h->rowptr = rowptr; h->col = col; h->val = val;
+    h->dtype = val_dtype; h->kind = kind; h->stream = (cudaStream_t)stream;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return fail(CLD_ERR_CUDA, "no CUDA device");
+    }
+    *out = h;
+    return CLD_OK;
+}
+
+void cld_destroy(cld_handle h) {
+    if (!h) return;
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    delete h;
+}
+
+cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!bytes || n < 0 || M < 1) return fail(CLD_ERR_INVALID, "bad arguments (n=%d, M=%d)", n, M);
+    *bytes = make_layout(h, n, M, with_grad).total;
+    return CLD_OK;
+}
+
+cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!dev_ptr) return fail(CLD_ERR_INVALID, "NULL workspace");
+    if (((uintptr_t)dev_ptr) % 256) return fail(CLD_ERR_INVALID, "workspace not 256-byte aligned");
+    const Layout L = make_layout(h, 0, 1, 0);
+    if (bytes < L.run) return fail(CLD_ERR_NOMEM, "workspace smaller than the fixed header");
+    h->ws = static_cast<char*>(dev_ptr);
+    h->ws_bytes = bytes;
+    h->ready = false;
+    uint32_t* flags = at<uint32_t>(h, L.flags);
+    CUDA_TRY(cudaMemsetAsync(flags, 0, 256, h->stream));
+    if (h->d > 0)
+        CUDA_TRY(launch_validate_csr(h->d, h->nnz, h->rowptr, h->col, h->val, (int)h->dtype, flags,
+                                     stream_grid(h), h->stream));
+    uint32_t f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (f & 1u) return fail(CLD_ERR_INVALID, "row pointers must start at 0, end at nnz and not decrease");
+    if (f & 2u) return fail(CLD_ERR_INVALID, "column index out of range [0, d)");
+    if (f & 4u) return fail(CLD_ERR_INVALID, "non-finite stored value");
+    if (h->kind == CLD_GENERAL && h->d > 0) {
+        CUDA_TRY(launch_transpose(h->d, h->nnz, h->rowptr, h->col, h->val, value_size(h->dtype),
+                                  at<int64_t>(h, L.rowptrT), at<int32_t>(h, L.colT), at<void>(h, L.valT),
+                                  at<int64_t>(h, L.tscratch), stream_grid(h), h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    if (h->have_interval)
+        CUDA_TRY(launch_set_params(at<Params>(h, L.params), h->a, h->b, h->stream));
+    h->ready = true;
+    return CLD_OK;
+}
+
+cld_status cld_set_interval(cld_handle h, double a, double b) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!(a > 0.0) || !(a < b) || !isfinite(a) || !isfinite(b))
+        return fail(CLD_ERR_INTERVAL, "interval must satisfy 0 < a < b (got [%g, %g])", a, b);
+    h->a = a;
+    h->b = b;
+    h->have_interval = true;
+    if (h->ws) {
+        const Layout L = make_layout(h, 0, 1, 0);
+        CUDA_TRY(launch_set_params(at<Params>(h, L.params), a, b, h->stream));
+    }
+    return CLD_OK;
+}
+
+cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a_out, double* b_out) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
+    if (h->d == 0) return fail(CLD_ERR_INTERVAL, "empty matrix has no spectrum");
+    if (lanczos_iters < 0 || lanczos_iters > 4000) return fail(CLD_ERR_INVALID, "lanczos_iters in [0, 4000]");
+    const Layout L = make_layout(h, 0, 1, 0);
+    if (lanczos_iters > 0 && h->ws_bytes < make_layout(h, 0, 1, 0).total)
+        return fail(CLD_ERR_NOMEM, "workspace too small for the Lanczos pass");
+    Params* prm = at<Params>(h, L.params);
+    uint32_t* flags = at<uint32_t>(h, L.flags);
+    CUDA_TRY(cudaMemsetAsync(flags, 0, 4, h->stream));
+    if (h->kind == CLD_SPD) {
+        CUDA_TRY(launch_gershgorin(h->d, h->rowptr, h->col, h->val, (int)h->dtype, at<double>(h, L.gpart),
+                                   L.ggrid, prm, flags, h->stream));
+        if (lanczos_iters > 0)
+            CUDA_TRY(launch_lanczos(h->d, h->rowptr, h->col, h->val, (int)h->dtype, lanczos_iters,
+                                    at<double>(h, L.lanczos), at<double>(h, L.lanczos) + 5 * h->d,
+                                    L.ggrid, prm, flags, h->stream));
+    } else {
+        CUDA_TRY(launch_general_bounds(h->d, h->rowptr, h->col, h->val, at<int64_t>(h, L.rowptrT),
+                                       at<int32_t>(h, L.colT), at<void>(h, L.valT), (int)h->dtype,
+                                       at<double>(h, L.gpart), L.ggrid, prm, flags, h->stream));
+    }
+    Params p{};
+    uint32_t f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&p, prm, sizeof(Params), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (a_out) *a_out = p.a;
+    if (b_out) *b_out = p.b;
+    if ((f & 0x100u) || !p.interval_ok) {
+        h->have_interval = false;
+        return fail(CLD_ERR_INTERVAL, "computed interval [%g, %g] is not a valid 0 < a < b", p.a, p.b);
+    }
+    h->a = p.a;
+    h->b = p.b;
+    h->have_interval = true;
+    return CLD_OK;
+}
+
+static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed) {
+    Params* prm = at<Params>(h, L.params);
+    double* T = at<double>(h, L.T);
+    double* tpart = at<double>(h, L.tpart);
+    uint32_t* vbits = at<uint32_t>(h, L.vbits);
+    float* W[3] = {at<float>(h, L.W[0]), at<float>(h, L.W[1]), at<float>(h, L.W[2])};
+    float* Y = h->kind == CLD_GENERAL ? at<float>(h, L.Y) : nullptr;
+    const bool general = h->kind == CLD_GENERAL;
+    const int64_t* rpT = general ? at<int64_t>(h, L.rowptrT) : h->rowptr;
+    const int32_t* colT = general ? at<int32_t>(h, L.colT) : h->col;
+    const void* valT = general ? at<void>(h, L.valT) : h->val;
+    int launches = 0, step_launches = 0;
+    int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+    if (h->profiling) {
+        while ((int)h->ev.size() < 2 * npanels) {
+            cudaEvent_t e;
+            CUDA_TRY(cudaEventCreate(&e));
+            h->ev.push_back(e);
+        }
+    }
+    CUDA_TRY(launch_set_seed(prm, seed, h->stream));
+    ++launches;
+    for (int pk = 0; pk < npanels; ++pk) {
+        const int pbase = pk * kMaxPanel;
+        const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
+        CUDA_TRY(launch_probe_bits(h->d, L.nw, (uint32_t)pk, prm, vbits, L.ggrid, h->stream));
+        ++launches;
+        StepArgs a{};
+        a.d = h->d;
+        a.vbits = vbits;
+        a.prm = prm;
+        a.mreal = mreal;
+        for (int j = 0; j < n; ++j) {
+            // w_{j+1} lives in W[(j+1) % 3]; w_j in W[j % 3] (j >= 1); w_0 = v.
+            if (h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
+            const float* wj = j >= 1 ? W[j % 3] : nullptr;
+            const float* wjm = j >= 2 ? W[(j - 1) % 3] : nullptr;
+            float* wout = W[(j + 1) % 3];
+            a.tpart = tpart + (size_t)j * L.grid * L.panel;
+            StepKind kind;
+            if (general) {
+                // y = C w_j, then w_{j+1} from C^T y
+                StepArgs p = a;
+                p.rowptr = h->rowptr; p.col = h->col; p.val = h->val;
+                p.x = wj; p.out = Y;
+                CUDA_TRY(launch_step(L.panel, (int)h->dtype, j == 0 ? kProdBits : kProdFloat, L.grid,
+                                     h->stream, p));
+                ++launches;
+                a.rowptr = rpT; a.col = colT; a.val = valT;
+                a.x = Y; a.own = wj; a.wprev = wjm; a.out = wout;
+                kind = j == 0 ? kStepFirstFromFloat : j == 1 ? kStepSecond : kStepGeneral;
+            } else {
+                a.rowptr = h->rowptr; a.col = h->col; a.val = h->val;
+                a.x = wj; a.own = wj; a.wprev = wjm; a.out = wout;
+                kind = j == 0 ? kStepFirst : j == 1 ? kStepSecond : kStepGeneral;
+            }
+            CUDA_TRY(launch_step(L.panel, (int)h->dtype, kind, L.grid, h->stream, a));
+            ++launches;
+            if (j >= 2) ++step_launches;
+        }
+        if (h->profiling && n >= 3) CUDA_TRY(cudaEventRecord(h->ev[2 * pk + 1], h->stream));
+        if (n > 0) {
+            CUDA_TRY(launch_reduce_moments(tpart, n, L.grid, L.panel, mreal, M, pbase, T, h->stream));
+            ++launches;
+        }
+    }
+    CUDA_TRY(launch_finalize(n, M, h->d, general ? 1 : 0, prm, T, at<double>(h, L.coeffs),
+                             at<double>(h, L.coef_scratch), at<double>(h, L.gamma_p),
+                             at<Result>(h, L.result), h->stream));
+    ++launches;
+    h->last_total_launches = launches;
+    h->last_step_launches = step_launches;
+    return CLD_OK;
+}
+
+cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
+                        double* stderr_out, double* moments_out) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (n < 0 || M < 1) return fail(CLD_ERR_INVALID, "need n >= 0 and M >= 1 (n=%d, M=%d)", n, M);
+    if (n > 100000) return fail(CLD_ERR_INVALID, "degree n > 100000 is not supported");
+    if (!logdet_out) return fail(CLD_ERR_INVALID, "logdet_out is NULL");
+    if (!h->have_interval) return fail(CLD_ERR_INTERVAL, "no spectral interval set");
+    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
+    const Layout L = make_layout(h, n, M, 0);
+    if (h->ws_bytes < L.total)
+        return fail(CLD_ERR_NOMEM, "workspace has %zu bytes, %zu needed", h->ws_bytes, L.total);
+    h->last_n = -1;
+    if (h->d == 0) {
+        *logdet_out = 0.0;
+        if (stderr_out) *stderr_out = 0.0;
+        if (moments_out) memset(moments_out, 0, sizeof(double) * (size_t)(n + 1) * M);
+        h->last_total_launches = h->last_step_launches = 0;
+        return CLD_OK;
+    }
+    cld_status st = enqueue_estimate(h, L, n, M, seed);
+    if (st != CLD_OK) return st;
+    Result r{};
+    CUDA_TRY(cudaMemcpyAsync(&r, at<Result>(h, L.result), sizeof(Result), cudaMemcpyDeviceToHost,
+                             h->stream));
+    if (moments_out)
+        CUDA_TRY(cudaMemcpyAsync(moments_out, at<double>(h, L.T), sizeof(double) * (size_t)(n + 1) * M,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->profiling && n >= 3) {
+        float total = 0.f;
+        const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+        for (int pk = 0; pk < npanels; ++pk) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2 * pk], h->ev[2 * pk + 1]));
+            total += ms;
+        }
+        h->last_step_ms = total;
+    } else {
+        h->last_step_ms = 0.f;
+    }
+    *logdet_out = r.logdet;
+    if (stderr_out) *stderr_out = r.stderr_;
+    h->last_n = n;
+    h->last_M = M;
+    if (r.spectrum_bad)
+        return fail(CLD_ERR_SPECTRUM,
+                    "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]", r.max_ratio,
+                    h->a, h->b);
+    return CLD_OK;
+}
+
+cld_status cld_last_details(cld_handle h, double* coeffs_out, double* gamma_p_out) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (h->last_n < 0) return fail(CLD_ERR_INVALID, "no completed estimate");
+    const Layout L = make_layout(h, h->last_n, h->last_M, 0);
+    if (coeffs_out)
+        CUDA_TRY(cudaMemcpyAsync(coeffs_out, at<double>(h, L.coeffs), sizeof(double) * (h->last_n + 1),
+                                 cudaMemcpyDeviceToHost, h->stream));
+    if (gamma_p_out)
+        CUDA_TRY(cudaMemcpyAsync(gamma_p_out, at<double>(h, L.gamma_p), sizeof(double) * h->last_M,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return CLD_OK;
+}
+
+cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out, float* dvalues_dev) {
+    (void)n; (void)M; (void)seed; (void)logdet_out; (void)dvalues_dev;
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    return fail(CLD_ERR_UNSUPPORTED, "cld_grad is not built yet");
+}
+
+cld_status cld_host_workspace_size(int64_t d, int64_t nnz, cld_dtype val_dtype, int n, int M,
+                                   size_t* bytes) {
+    if (!bytes || d < 0 || nnz < 0 || n < 0 || M < 1) return fail(CLD_ERR_INVALID, "bad arguments");
+    if (val_dtype != CLD_F32 && val_dtype != CLD_BF16 && val_dtype != CLD_F64)
+        return fail(CLD_ERR_INVALID, "unknown value dtype");
+    cld_ctx tmp;
+    tmp.d = d; tmp.nnz = nnz; tmp.dtype = val_dtype; tmp.kind = CLD_GENERAL;  // largest layout
+    if (cudaGetDevice(&tmp.device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&tmp.sms, cudaDevAttrMultiProcessorCount, tmp.device) != cudaSuccess)
+        return fail(CLD_ERR_CUDA, "no CUDA device");
+    const size_t csr = align_up((size_t)(d + 1) * 8) + align_up((size_t)nnz * 4) +
+                       align_up((size_t)nnz * value_size(val_dtype));
+    *bytes = csr + make_layout(&tmp, n, M, 0).total;
+    return CLD_OK;
+}
+
+cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* rowptr_host,
+                               const int32_t* col_host, const void* val_host, cld_dtype val_dtype,
+                               cld_kind kind, double a, double b, int n, int M, uint64_t seed,
+                               void* workspace_dev, size_t workspace_bytes, void* stream,
+                               double* logdet_out, double* stderr_out) {
+    size_t need = 0;
+    cld_status st = cld_host_workspace_size(d, nnz, val_dtype, n, M, &need);
+    if (st) return st;
+    if (!workspace_dev || workspace_bytes < need)
+        return fail(CLD_ERR_NOMEM, "host-input workspace needs %zu bytes", need);
+    if (((uintptr_t)workspace_dev) % 256) return fail(CLD_ERR_INVALID, "workspace not 256-byte aligned");
+    if (!rowptr_host || (nnz > 0 && (!col_host || !val_host))) return fail(CLD_ERR_INVALID, "NULL CSR array");
+    cudaStream_t s = (cudaStream_t)stream;
+    char* w = static_cast<char*>(workspace_dev);
+    const size_t o_col = align_up((size_t)(d + 1) * 8);
+    const size_t o_val = o_col + align_up((size_t)nnz * 4);
+    const size_t o_ws = o_val + align_up((size_t)nnz * value_size(val_dtype));
+    CUDA_TRY(cudaMemcpyAsync(w, rowptr_host, (size_t)(d + 1) * 8, cudaMemcpyHostToDevice, s));
+    if (nnz > 0) {
+        CUDA_TRY(cudaMemcpyAsync(w + o_col, col_host, (size_t)nnz * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(w + o_val, val_host, (size_t)nnz * value_size(val_dtype),
+                                 cudaMemcpyHostToDevice, s));
+    }
+    cld_handle h = nullptr;
+    st = cld_create_csr(&h, d, nnz, reinterpret_cast<int64_t*>(w), reinterpret_cast<int32_t*>(w + o_col),
+                        w + o_val, val_dtype, kind, stream);
+    if (st) return st;
+    st = cld_set_interval(h, a, b);
+    if (!st) st = cld_set_workspace(h, w + o_ws, workspace_bytes - o_ws);
+    if (!st) st = cld_estimate(h, n, M, seed, logdet_out, stderr_out, nullptr);
+    cld_destroy(h);
+    return st;
+}
+
+cld_status cld_set_profiling(cld_handle h, int on) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    h->profiling = on != 0;
+    return CLD_OK;
+}
+
+cld_status cld_last_timing(cld_handle h, float* step_ms, int* step_launches, int* total_launches) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (step_ms) *step_ms = h->last_step_ms;
+    if (step_launches) *step_launches = h->last_step_launches;
+    if (total_launches) *total_launches = h->last_total_launches;
+    return CLD_OK;
+}
+
+cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row, int* ctas,
+                             int* threads) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (M < 1) return fail(CLD_ERR_INVALID, "M >= 1");
+    const Layout L = make_layout(h, 1, M, 0);
+    if (panel) *panel = L.panel;
+    if (lanes_per_row) *lanes_per_row = L.panel / 4;
+    if (ctas) *ctas = L.grid;
+    if (threads) *threads = kThreads;
+    return CLD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,135 @@
+// Internal declarations shared by the libcld translation units.
+//
+// Device-side pieces of the Chebyshev-Hutchinson estimator (Han, Malioutov,
+// Shin, arXiv 1503.06394): the Rademacher probe stream, the parameter block
+// the kernels read, the value loaders for FP32 / BF16 / FP64 storage, and the
+// host-callable launchers implemented in step_*.cu and aux.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cld {
+
+constexpr int kThreads = 256;   // threads per CTA of every streaming kernel
+constexpr int kMaxPanel = 128;  // probes per pass (counter word 2 = panel index)
+
+// Parameter block in the workspace; written by the host (cudaMemcpyAsync) or
+// by the interval kernels, read by every kernel of a run.  Keeping it on the
+// device lets the captured graph of a run stay valid when [a, b] or the seed
+// change.
+struct Params {
+    double a, b;         // spectral interval [a, b]
+    float scale;         // 2 / (b - a)
+    float shift;         // (a + b) / (b - a)
+    uint32_t key_lo;     // Philox key = probe seed
+    uint32_t key_hi;
+    int32_t interval_ok; // 1 once a and b are valid
+    int32_t pad;
+};
+
+// Result block in the workspace, written by the final kernel.
+struct Result {
+    double logdet;
+    double stderr_;
+    double max_ratio;    // max_{j,p} |t_{j,p}| / d
+    int32_t spectrum_bad;
+    int32_t pad;
+};
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of
+// (c0..c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1, lo(M0 c0))
+// with the key bumped by the two Weyl constants after each round.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+        uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// +-1 (or 0 for a padded probe) for the four probes whose sign bits sit at
+// bits [sh, sh+4) of `word`.  bit = 1 -> -1.0f; mask_q = 0 -> 0.0f.
+__device__ __forceinline__ float4 signs4(uint32_t word, int sh, float4 mask) {
+    uint32_t b = word >> sh;
+    float4 s;
+    s.x = __uint_as_float(0x3f800000u | ((b & 1u) << 31)) * mask.x;
+    s.y = __uint_as_float(0x3f800000u | (((b >> 1) & 1u) << 31)) * mask.y;
+    s.z = __uint_as_float(0x3f800000u | (((b >> 2) & 1u) << 31)) * mask.z;
+    s.w = __uint_as_float(0x3f800000u | (((b >> 3) & 1u) << 31)) * mask.w;
+    return s;
+}
+
+// ------------------------------------------------------------------ values
+struct bf16_t { uint16_t bits; };
+
+__device__ __forceinline__ float load_val(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float load_val(const double* p) { return (float)__ldg(p); }
+__device__ __forceinline__ float load_val(const bf16_t* p) {
+    uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float(((uint32_t)b) << 16);
+}
+__device__ __forceinline__ double load_val_f64(const float* p) { return (double)__ldg(p); }
+__device__ __forceinline__ double load_val_f64(const double* p) { return __ldg(p); }
+__device__ __forceinline__ double load_val_f64(const bf16_t* p) {
+    uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(p));
+    return (double)__uint_as_float(((uint32_t)b) << 16);
+}
+
+// ------------------------------------------------------------------ step launch
+// One recurrence step over one probe panel.  The template modes are:
+//   gather: 0 = gather rows of a float buffer `x`; 1 = gather probe signs
+//   prev:   0 = first step (no w_{j-1}; own row is v), 1 = w_{j-1} is v,
+//           2 = w_{j-1} is the float buffer `wprev`
+//   epi:    0 = store the plain product y = X x;
+//           1 = store w_{j+1} = f(scale, shift, X x, own, prev) and reduce
+//               t_{j+1,p} = sum_i v[i,p] w_{j+1}[i,p] into per-CTA partials
+struct StepArgs {
+    int64_t d;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const void* val;
+    const float* x;          // gather source (gather == 0)
+    const float* own;        // w_j rows for the shift term (prev != 0)
+    const float* wprev;      // w_{j-1} (prev == 2)
+    float* out;              // w_{j+1} (epi 1) or y (epi 0)
+    const uint32_t* vbits;   // d x nw sign words of the panel
+    double* tpart;           // [grid][panel] partial moments (epi 1)
+    const Params* prm;
+    int mreal;               // real probes in this panel
+};
+
+enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
+                kStepFirstFromFloat = 5 };
+
+// Launches one step with `grid` CTAs on `stream`.  panel in {4,8,...,128}.
+cudaError_t launch_step(int panel, int dtype, StepKind kind, int grid, cudaStream_t stream,
+                        const StepArgs& a);
+// Resident CTAs per SM of the general step kernel (for grid sizing).
+int step_ctas_per_sm(int panel, int dtype);
+// Number of sign words per row for a panel width.
+inline int sign_words(int panel) { return panel <= 32 ? 1 : panel / 32; }
+
+// ------------------------------------------------------------------ aux launches (aux.cu)
+cudaError_t launch_probe_bits(int64_t d, int nw, uint32_t panel_index, const Params* prm,
+                              uint32_t* vbits, int grid, cudaStream_t s);
+cudaError_t launch_reduce_moments(const double* tpart, int nsteps, int grid_blocks, int panel,
+                                  int mreal, int M, int pbase, double* T, cudaStream_t s);
+cudaError_t launch_finalize(int n, int M, int64_t d, int general, const Params* prm,
+                            double* T, double* coeffs, double* coef_scratch, double* gamma_p,
+                            Result* res, cudaStream_t s);
+cudaError_t launch_validate_csr(int64_t d, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                                const void* val, int dtype, uint32_t* flags, int grid,
+                                cudaStream_t s);
+cudaError_t launch_gershgorin(int64_t d, const int64_t* rowptr, const int32_t* col,
+                              const void* val, int dtype, double* partial, int grid,
+                              Params* prm, uint32_t* flags, cudaStream_t s);
+cudaError_t launch_set_params(Params* prm, double a, double b, cudaStream_t s);
+
+}  // namespace cld

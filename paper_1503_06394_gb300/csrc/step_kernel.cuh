@@ -1,0 +1,209 @@
+// Fused Chebyshev recurrence step (the hot loop of Algorithm 1, Sec. 2.2).
+//
+// One launch advances all probes of a panel by one degree:
+//   w_{j+1} = 2 (scale * (X w_j) - shift * w_j) - w_{j-1},
+//   scale = 2/(b-a), shift = (a+b)/(b-a), i.e. 2 At w_j - w_{j-1} with
+//   At = (2X - (a+b) I)/(b-a) applied on the fly (X is never rewritten),
+// and reduces t_{j+1,p} = v_p^T w_{j+1} for every probe p of the panel.
+//
+// Layout: the recurrence vectors of a panel are a d x P row-major FP32 block
+// (probe index fastest, P in {4,...,128}).  A row of X is owned by a group of
+// P/4 lanes; lane l of the group holds probes 4l..4l+3 as one float4, so every
+// stored entry (i, k) costs one contiguous P*4-byte gather of row k of w_j
+// (128 B, one L2 line, at P = 32).  Rows are dealt to groups round-robin
+// (row = group id + r * #groups) so a warp's own-row loads and stores are
+// contiguous.  Sign bits of the probes are read from a packed d x nw array
+// (1 bit per probe) instead of materialising v.
+//
+// Moments: each lane accumulates its four v * w_{j+1} products in FP32 over
+// its rows (every product is an exact sign flip), converts to FP64 and the
+// CTA reduces them in a fixed order to one partial per probe; a later kernel
+// sums the partials over CTAs in a fixed order, so results are deterministic.
+#pragma once
+
+#include "cld_internal.cuh"
+
+namespace cld {
+
+__device__ __forceinline__ float4 ldg4(const float* p) {
+    return __ldg(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ float4 ldcs4(const float* p) {
+    return __ldcs(reinterpret_cast<const float4*>(p));
+}
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+
+// GATHER: 0 float rows of args.x, 1 probe signs.  PREV: 0 none, 1 v, 2 args.wprev.
+// EPI: 0 plain product, 1 recurrence + moments.
+template <int MP, typename VT, int GATHER, int PREV, int EPI>
+__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
+    constexpr int LPR = MP / 4;          // lanes per row
+    constexpr int GPW = 32 / LPR;        // rows per warp
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    constexpr int WPB = kThreads / 32;
+    constexpr int U = 4;                 // stored entries in flight per group
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int lig = lane % LPR;
+    const int g_in_w = lane / LPR;
+    const int64_t gid = ((int64_t)blockIdx.x * WPB + warp) * GPW + g_in_w;
+    const int64_t ngroups = (int64_t)gridDim.x * WPB * GPW;
+    const int64_t d = args.d;
+
+    const int p0 = 4 * lig;
+    const int wsel = p0 >> 5;
+    const int bsh = p0 & 31;
+    const float4 mask = make_float4(p0 < args.mreal ? 1.f : 0.f, p0 + 1 < args.mreal ? 1.f : 0.f,
+                                    p0 + 2 < args.mreal ? 1.f : 0.f, p0 + 3 < args.mreal ? 1.f : 0.f);
+
+    const int64_t* __restrict__ rowptr = args.rowptr;
+    const int32_t* __restrict__ col = args.col;
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const uint32_t* __restrict__ vbits = args.vbits;
+
+    float scale = 1.f, shift = 0.f;
+    if (EPI == 1) {
+        scale = args.prm->scale;
+        shift = args.prm->shift;
+    }
+
+    float4 tacc = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    for (int64_t row = gid; row < d; row += ngroups) {
+        const int64_t k0 = __ldg(rowptr + row);
+        const int64_t k1 = __ldg(rowptr + row + 1);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t k = k0; k < k1; k += U) {
+            int c[U];
+            float a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = k + u < k1;
+                c[u] = ok ? __ldg(col + k + u) : -1;
+                a[u] = ok ? load_val(val + k + u) : 0.f;
+            }
+            float4 xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] >= 0) {
+                    if (GATHER == 1)
+                        xv[u] = signs4(__ldg(vbits + (int64_t)c[u] * NW + wsel), bsh, mask);
+                    else
+                        xv[u] = ldg4(args.x + (int64_t)c[u] * MP + p0);
+                } else {
+                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc.x = fmaf(a[u], xv[u].x, acc.x);
+                acc.y = fmaf(a[u], xv[u].y, acc.y);
+                acc.z = fmaf(a[u], xv[u].z, acc.z);
+                acc.w = fmaf(a[u], xv[u].w, acc.w);
+            }
+        }
+        float4 res;
+        if (EPI == 0) {
+            res = acc;
+        } else {
+            const float4 v = signs4(__ldg(vbits + row * NW + wsel), bsh, mask);
+            const float4 own = (PREV == 0) ? v : ldg4(args.own + row * MP + p0);
+            float4 y;
+            y.x = fmaf(scale, acc.x, -shift * own.x);
+            y.y = fmaf(scale, acc.y, -shift * own.y);
+            y.z = fmaf(scale, acc.z, -shift * own.z);
+            y.w = fmaf(scale, acc.w, -shift * own.w);
+            if (PREV == 0) {
+                res = y;
+            } else {
+                const float4 pv = (PREV == 1) ? v : ldcs4(args.wprev + row * MP + p0);
+                res.x = fmaf(2.f, y.x, -pv.x);
+                res.y = fmaf(2.f, y.y, -pv.y);
+                res.z = fmaf(2.f, y.z, -pv.z);
+                res.w = fmaf(2.f, y.w, -pv.w);
+            }
+            tacc.x = fmaf(v.x, res.x, tacc.x);
+            tacc.y = fmaf(v.y, res.y, tacc.y);
+            tacc.z = fmaf(v.z, res.z, tacc.z);
+            tacc.w = fmaf(v.w, res.w, tacc.w);
+        }
+        st4(args.out + row * MP + p0, res);
+    }
+
+    if (EPI == 1) {
+        __shared__ double red[WPB][MP];
+        double t0 = tacc.x, t1 = tacc.y, t2 = tacc.z, t3 = tacc.w;
+#pragma unroll
+        for (int off = LPR; off < 32; off <<= 1) {
+            t0 += __shfl_xor_sync(0xffffffffu, t0, off);
+            t1 += __shfl_xor_sync(0xffffffffu, t1, off);
+            t2 += __shfl_xor_sync(0xffffffffu, t2, off);
+            t3 += __shfl_xor_sync(0xffffffffu, t3, off);
+        }
+        if (g_in_w == 0) {
+            red[warp][p0 + 0] = t0;
+            red[warp][p0 + 1] = t1;
+            red[warp][p0 + 2] = t2;
+            red[warp][p0 + 3] = t3;
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < MP; p += kThreads) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < WPB; ++w) s += red[w][p];
+            args.tpart[(int64_t)blockIdx.x * MP + p] = s;
+        }
+    }
+}
+
+template <int MP, typename VT>
+cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
+    switch (kind) {
+        case kStepFirst: step_kernel<MP, VT, 1, 0, 1><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepSecond: step_kernel<MP, VT, 0, 1, 1><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepGeneral: step_kernel<MP, VT, 0, 2, 1><<<grid, kThreads, 0, s>>>(a); break;
+        case kProdBits: step_kernel<MP, VT, 1, 0, 0><<<grid, kThreads, 0, s>>>(a); break;
+        case kProdFloat: step_kernel<MP, VT, 0, 0, 0><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepFirstFromFloat: step_kernel<MP, VT, 0, 0, 1><<<grid, kThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename VT>
+cudaError_t launch_step_vt(int panel, StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
+    switch (panel) {
+        case 4: return launch_step_mp<4, VT>(kind, grid, s, a);
+        case 8: return launch_step_mp<8, VT>(kind, grid, s, a);
+        case 16: return launch_step_mp<16, VT>(kind, grid, s, a);
+        case 32: return launch_step_mp<32, VT>(kind, grid, s, a);
+        case 64: return launch_step_mp<64, VT>(kind, grid, s, a);
+        case 128: return launch_step_mp<128, VT>(kind, grid, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int MP, typename VT>
+int ctas_per_sm_mp() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1>, kThreads, 0) !=
+        cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+template <typename VT>
+int ctas_per_sm_vt(int panel) {
+    switch (panel) {
+        case 4: return ctas_per_sm_mp<4, VT>();
+        case 8: return ctas_per_sm_mp<8, VT>();
+        case 16: return ctas_per_sm_mp<16, VT>();
+        case 32: return ctas_per_sm_mp<32, VT>();
+        case 64: return ctas_per_sm_mp<64, VT>();
+        case 128: return ctas_per_sm_mp<128, VT>();
+        default: return 1;
+    }
+}
+
+}  // namespace cld

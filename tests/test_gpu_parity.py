@@ -1,0 +1,234 @@
+"""GPU parity: libcld (through the C ABI) against the CPU FP64 oracle on
+identical probes.  Tolerance: the estimate within 1e-5 relative (FP32 and FP64
+storage) or 2e-3 (BF16 storage, against the oracle on the original values);
+moments within the FP32-recurrence bound of gpu_common.moment_tol."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_common import moment_tol, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+def run_gpu(B, dtype, a, b, n, M, seed=0, moments=True):
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    stored, _ = B.stored(dtype)
+    m = CsrLogdet(B.rowptr, B.col, stored, dtype=dtype)
+    m.set_interval(a, b)
+    r = m.estimate(n, M, seed, moments=moments, details=True)
+    m.close()
+    return r
+
+
+def check(B, dtype, n, M, seed=0, probes=None, interval=None, tol_gamma=1e-5):
+    _, v64 = B.stored(dtype)
+    a, b = interval if interval is not None else oracle.gershgorin(B.rowptr, B.col, v64)
+    if not b - a > 1e-9 * abs(b):  # one-point spectrum (d = 1): widen
+        a, b = 0.5 * a, 1.5 * b
+    r = run_gpu(B, dtype, a, b, n, M, seed)
+    ref = oracle.estimate(B.rowptr, B.col, v64, a, b, n, M, seed=seed, probes=probes)
+    cols = np.arange(M) if probes is None else np.asarray(probes)
+    dt = np.abs(r["t"][:, cols] - ref["t"])
+    assert np.all(dt <= moment_tol(B.d, n)), "moment mismatch: max %g at %s" % (dt.max(), np.unravel_index(dt.argmax(), dt.shape))
+    if probes is None:
+        assert abs(r["logdet"] - ref["gamma"]) <= tol_gamma * abs(ref["gamma"]) + 1e-9
+        np.testing.assert_allclose(r["c"], ref["c"], rtol=1e-12, atol=1e-13)
+        np.testing.assert_allclose(r["gamma_p"], ref["gamma_p"], rtol=1e-5, atol=1e-6 * B.d)
+        assert abs(r["stderr"] - ref["stderr"]) <= 1e-3 * ref["stderr"] + 1e-9 if M > 1 else True
+    return r, ref
+
+
+@pytest.mark.parametrize("d", [1, 31, 32, 33, 1000, 2048])
+@pytest.mark.parametrize("M", [1, 16, 30, 64])
+def test_parity_shapes(torch, d, M):
+    B = workloads.sparse_random_spd(d, 3, 100 + d)
+    check(B, "f32", 12, M, seed=d + M)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_parity_low_degree(torch, n):
+    B = workloads.sparse_random_spd(777, 3, 5)
+    check(B, "f32", n, 20, seed=9)
+
+
+@pytest.mark.parametrize("M", [4, 8, 128, 130, 300])
+def test_parity_panels(torch, M):
+    """M up to 128 is one panel (padded to a power of two); beyond, panels of 128."""
+    B = workloads.sparse_random_spd(600, 3, 11)
+    check(B, "f32", 10, M, seed=3)
+
+
+def test_parity_ragged_rows(torch):
+    """Rows from 1 to ~60 stored entries (ragged tails of the 4-entry unrolled loop)."""
+    rng = np.random.default_rng(0)
+    d = 3000
+    deg = rng.integers(0, 30, size=d)
+    rows = np.repeat(np.arange(d), deg)
+    cols = rng.integers(0, d, size=rows.size)
+    off = rows != cols
+    rows, cols = rows[off], cols[off]
+    vals = rng.standard_normal(rows.size)
+    r = np.concatenate([rows, cols])
+    c = np.concatenate([cols, rows])
+    v = np.concatenate([vals, vals])
+    Bo = workloads._coo_to_csr(d, r, c, v, "ragged")
+    R = workloads._abs_row_sums(d, Bo)
+    B = workloads._with_diagonal(d, Bo, R + 0.5, "ragged")
+    lens = np.diff(B.rowptr)
+    assert lens.min() == 1 and lens.max() > 40
+    check(B, "f32", 15, 32, seed=4)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+def test_config0_full(torch, dtype):
+    """Sparse random SPD, d=2048, n=30, M=30, probe seed 0; error vs Cholesky reported."""
+    cfg = workloads.CONFIGS[0]
+    B = workloads.make(cfg)
+    r, ref = check(B, dtype, cfg["n"], cfg["M"], seed=cfg["probe_seed"])
+    _, v64 = B.stored(dtype)
+    exact = oracle.logdet_cholesky(workloads.Csr(B.rowptr, B.col, v64).dense())
+    rel_exact = abs(r["logdet"] - exact) / abs(exact)
+    print("config0 %s: gpu=%.6f oracle=%.6f exact=%.6f rel_vs_oracle=%.2e rel_vs_exact=%.2e stderr=%.3f" % (
+        dtype, r["logdet"], ref["gamma"], exact, abs(r["logdet"] - ref["gamma"]) / abs(ref["gamma"]),
+        rel_exact, r["stderr"]))
+    assert abs(r["logdet"] - exact) <= 5 * r["stderr"] + 1e-3 * abs(exact)
+
+
+def test_bf16_storage(torch):
+    """BF16 values: parity with the oracle on the BF16 values, and within 2e-3
+    of the oracle on the original FP64 values."""
+    B = workloads.sparse_random_spd(4000, 3, 21)
+    n, M = 30, 32
+    _, v16 = B.stored("bf16")
+    lo, hi = oracle.gershgorin(B.rowptr, B.col, B.val)
+    lo16, hi16 = oracle.gershgorin(B.rowptr, B.col, v16)
+    a, b = 0.98 * min(lo, lo16), 1.0
+    r, _ = check(B, "bf16", n, M, interval=(a, b))
+    ref64 = oracle.estimate(B.rowptr, B.col, B.val, a, b, n, M, seed=0)
+    assert abs(r["logdet"] - ref64["gamma"]) <= 2e-3 * abs(ref64["gamma"])
+
+
+def test_config1_full_sampled(torch):
+    """GMRF 1000x1000 grid (d=1e6), n=50, M=64: all moments of probes 0, 37 and 63
+    against the oracle; the estimate against the closed form within 5 stderr."""
+    cfg = workloads.CONFIGS[1]
+    B = workloads.make(cfg)
+    a, b = cfg["kappa2"], cfg["kappa2"] + 8.0
+    r, ref = check(B, "f32", cfg["n"], cfg["M"], seed=0, probes=[0, 37, 63], interval=(a, b))
+    exact = oracle.grid_laplacian_logdet(cfg["N"], cfg["kappa2"])
+    print("config1: gpu=%.3f exact=%.3f rel=%.2e stderr=%.3f" % (r["logdet"], exact,
+                                                                 abs(r["logdet"] - exact) / exact, r["stderr"]))
+    assert abs(r["logdet"] - exact) <= 5 * r["stderr"]
+    # the oracle's probe-37 estimate equals the GPU's per-probe estimate
+    assert abs(r["gamma_p"][37] - ref["gamma_p"][1]) <= 1e-5 * abs(ref["gamma_p"][1])
+
+
+def test_degenerate_inputs(torch):
+    from paper_1503_06394_gb300 import CldError, CsrLogdet
+    from paper_1503_06394_gb300 import _binding as Bd
+
+    # empty matrix: log det of a 0 x 0 matrix is 0
+    m = CsrLogdet(np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0, np.float32))
+    m.set_interval(0.5, 1.0)
+    assert m.estimate(5, 3)["logdet"] == 0.0
+    m.close()
+    # 1 x 1: exact for any probes: sum_j c_j T_j(mu) = p_n(lambda)
+    m = CsrLogdet(np.array([0, 1], np.int64), np.array([0], np.int32), np.array([0.3], np.float32))
+    m.set_interval(0.1, 1.0)
+    r = m.estimate(40, 4)
+    assert abs(r["logdet"] - np.log(np.float32(0.3))) < 1e-5
+    m.close()
+    B = workloads.sparse_random_spd(100, 3, 1)
+    v32, _ = B.stored("f32")
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    for a, b in [(0.0, 1.0), (-1.0, 1.0), (0.5, 0.5), (0.9, 0.1), (np.nan, 1.0), (0.1, np.inf)]:
+        with pytest.raises(CldError) as e:
+            m.set_interval(a, b)
+        assert e.value.status == Bd.CLD_ERR_INTERVAL
+    with pytest.raises(CldError) as e:
+        m.estimate(10, 4)  # no interval yet
+    assert e.value.status == Bd.CLD_ERR_INTERVAL
+    m.set_interval(0.01, 1.0)
+    for n, M in [(-1, 4), (5, 0)]:
+        with pytest.raises(CldError) as e:
+            m.estimate(n, M)
+        assert e.value.status == Bd.CLD_ERR_INVALID
+    # interval that misses the top of the spectrum -> CLD_ERR_SPECTRUM
+    lo, hi = oracle.gershgorin(B.rowptr, B.col, B.val)
+    m.set_interval(lo, 0.4 * hi)
+    with pytest.raises(CldError) as e:
+        m.estimate(60, 8)
+    assert e.value.status == Bd.CLD_ERR_SPECTRUM
+    m.close()
+
+
+def test_malformed_csr_rejected(torch):
+    from paper_1503_06394_gb300 import CldError, CsrLogdet
+    from paper_1503_06394_gb300 import _binding as Bd
+
+    B = workloads.sparse_random_spd(50, 3, 2)
+    v32, _ = B.stored("f32")
+    bad_col = B.col.copy()
+    bad_col[7] = 50
+    bad_val = v32.copy()
+    bad_val[3] = np.nan
+    bad_ptr = B.rowptr.copy()
+    bad_ptr[10], bad_ptr[11] = bad_ptr[11], bad_ptr[10]
+    for rp, c, v in [(B.rowptr, bad_col, v32), (B.rowptr, B.col, bad_val), (bad_ptr, B.col, v32)]:
+        m = CsrLogdet(rp, c, v)
+        with pytest.raises(CldError) as e:
+            m.reserve(5, 4)
+        assert e.value.status == Bd.CLD_ERR_INVALID
+        m.close()
+
+
+def test_gershgorin_and_lanczos_interval(torch):
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    B = workloads.sparse_random_spd(2048, 3, 1000)
+    v32, v64 = B.stored("f32")
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    a, b = m.auto_interval(0)
+    lo, hi = oracle.gershgorin(B.rowptr, B.col, v64)
+    assert abs(a - lo) <= 1e-12 * abs(lo) and abs(b - hi) <= 1e-12 * abs(hi)
+    a2, b2 = m.auto_interval(40)
+    ev = np.linalg.eigvalsh(workloads.Csr(B.rowptr, B.col, v64).dense())
+    assert a2 == a and ev[-1] <= b2 <= b
+    assert b2 < 0.8 * b  # Lanczos tightens the Gershgorin end (0.99 -> ~0.62)
+    r = m.estimate(30, 30, 0)
+    ref = oracle.estimate(B.rowptr, B.col, v64, a2, b2, 30, 30, seed=0)
+    assert abs(r["logdet"] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
+    m.close()
+
+
+def test_host_entry_matches_device_entry(torch):
+    from paper_1503_06394_gb300 import logdet_host
+
+    B = workloads.sparse_random_spd(5000, 3, 8)
+    v32, v64 = B.stored("f32")
+    lo, hi = oracle.gershgorin(B.rowptr, B.col, v64)
+    r = run_gpu(B, "f32", lo, hi, 25, 32, seed=5, moments=False)
+    g, se = logdet_host(B.rowptr, B.col, v32, lo, hi, 25, 32, seed=5)
+    assert g == r["logdet"] and se == r["stderr"]
+
+
+def test_profiling_counts_launches(torch):
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    B = workloads.sparse_random_spd(20000, 3, 8)
+    v32, v64 = B.stored("f32")
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    m.auto_interval(0)
+    m.set_profiling(True)
+    m.estimate(20, 32, 0)
+    ms, steps, total = m.last_timing()
+    assert ms > 0 and steps == 18 and total == 20 + 4
+    m.close()

@@ -171,6 +171,21 @@ def test_sigma_max_bound(oracle_mod):
     assert s[-1] >= 1.0 - 1e-12  # Varah: diagonal dominance by 1 in rows and columns
 
 
+def test_dominance_margins_bound_sigma_min(oracle_mod):
+    """Sec. 3.2 via Varah: sigma_min(C)^2 >= alpha * beta for row/column dominant C."""
+    for seed in range(3):
+        C = workloads.nonsymmetric_dominant(200, 3, seed)
+        al, be = oracle_mod.dominance_margins(C.rowptr, C.col, C.val)
+        A = C.dense()
+        s = np.linalg.svd(A, compute_uv=False)
+        assert al >= 1.0 - 1e-12 and be >= 1.0 - 1e-12
+        assert s[-1] ** 2 >= al * be * (1 - 1e-12)
+        R = np.sum(np.abs(A), axis=1) - np.abs(np.diag(A))
+        S = np.sum(np.abs(A), axis=0) - np.abs(np.diag(A))
+        assert abs(al - np.min(np.abs(np.diag(A)) - R)) < 1e-12
+        assert abs(be - np.min(np.abs(np.diag(A)) - S)) < 1e-12
+
+
 def test_grid_closed_form(oracle_mod):
     for N in (1, 2, 6, 9):
         G = workloads.grid_gmrf(N, 0.1)
