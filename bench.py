@@ -110,8 +110,13 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def build_workload(cfg_id):
+def build_workload(cfg_id, d_override=None):
     cfg = dict(workloads.CONFIGS[cfg_id])
+    if d_override:
+        if cfg["kind"] == "grid_gmrf":
+            cfg["N"] = int(round(d_override ** 0.5))
+        else:
+            cfg["d"] = int(d_override)
     t0 = time.time()
     B = workloads.make(cfg)
     gen_s = time.time() - t0
@@ -147,7 +152,7 @@ def run_reference(args, rank, world):
     oracle.build()
     if rank != 0:
         return
-    cfg, B, interval, desc, _ = build_workload(args.config)
+    cfg, B, interval, desc, _ = build_workload(args.config, args.d)
     stored, v64 = B.stored(args.dtype)
     s_v = {"f32": 4, "bf16": 2, "f64": 8}[args.dtype]
     a, b = interval if interval is not None else oracle.gershgorin(B.rowptr, B.col, v64)
@@ -184,7 +189,7 @@ def run_ours(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    cfg, B, interval, desc, gen_s = build_workload(args.config)
+    cfg, B, interval, desc, gen_s = build_workload(args.config, args.d)
     stored, v64 = B.stored(args.dtype)
     s_v = {"f32": 4, "bf16": 2, "f64": 8}[args.dtype]
     n, M = cfg["n"], cfg["M"]
@@ -311,6 +316,7 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[0, 1, 2])
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--d", type=int, default=None, help="override the dimension (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

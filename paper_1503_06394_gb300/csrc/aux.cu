@@ -35,10 +35,7 @@ int step_ctas_per_sm(int panel, int dtype) {
 
 // ------------------------------------------------------------------ parameters
 __global__ void set_interval_kernel(Params* prm, double a, double b) {
-    prm->a = a;
-    prm->b = b;
-    prm->scale = (float)(2.0 / (b - a));
-    prm->shift = (float)((a + b) / (b - a));
+    set_affine(prm, a, b);
     prm->interval_ok = (a > 0.0 && a < b && isfinite(a) && isfinite(b)) ? 1 : 0;
 }
 
@@ -308,10 +305,7 @@ __global__ void gershgorin_final_kernel(const double* partial, int nblocks, Para
     }
     if (threadIdx.x == 0) {
         const double a = shl[0], b = shh[0];
-        prm->a = a;
-        prm->b = b;
-        prm->scale = (float)(2.0 / (b - a));
-        prm->shift = (float)((a + b) / (b - a));
+        set_affine(prm, a, b);
         const int ok = (a > 0.0 && a < b && isfinite(a) && isfinite(b)) ? 1 : 0;
         prm->interval_ok = ok;
         if (!ok) atomicOr(flags, 0x100u);

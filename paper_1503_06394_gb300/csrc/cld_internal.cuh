@@ -18,15 +18,31 @@ constexpr int kMaxPanel = 128;  // probes per pass (counter word 2 = panel index
 // by the interval kernels, read by every kernel of a run.  Keeping it on the
 // device lets the captured graph of a run stay valid when [a, b] or the seed
 // change.
+// scale = 2/(b-a) and shift = (a+b)/(b-a) are kept as FP32 hi + lo pairs
+// (hi = fl(x), lo = fl(x - hi)): a single FP32 constant would apply a
+// systematically shifted matrix, an error of order 2^-24 d in every moment;
+// the pair is exact to about 2^-48 and leaves only per-element rounding.
 struct Params {
     double a, b;         // spectral interval [a, b]
-    float scale;         // 2 / (b - a)
-    float shift;         // (a + b) / (b - a)
+    float scale_hi, scale_lo;
+    float shift_hi, shift_lo;
     uint32_t key_lo;     // Philox key = probe seed
     uint32_t key_hi;
     int32_t interval_ok; // 1 once a and b are valid
     int32_t pad;
 };
+
+__host__ __device__ inline void split_f32(double x, float* hi, float* lo) {
+    *hi = (float)x;
+    *lo = (float)(x - (double)*hi);
+}
+
+__host__ __device__ inline void set_affine(Params* p, double a, double b) {
+    p->a = a;
+    p->b = b;
+    split_f32(2.0 / (b - a), &p->scale_hi, &p->scale_lo);
+    split_f32((a + b) / (b - a), &p->shift_hi, &p->shift_lo);
+}
 
 // Result block in the workspace, written by the final kernel.
 struct Result {

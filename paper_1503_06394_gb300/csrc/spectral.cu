@@ -163,10 +163,7 @@ __global__ void general_bounds_final_kernel(const double* partial, int nb, Param
     }
     const double a = (amin > 0.0 && bmin > 0.0) ? amin * bmin : 0.0;
     const double b = rmax * cmax;
-    prm->a = a;
-    prm->b = b;
-    prm->scale = (float)(2.0 / (b - a));
-    prm->shift = (float)((a + b) / (b - a));
+    set_affine(prm, a, b);
     const int ok = (a > 0.0 && a < b && isfinite(a) && isfinite(b)) ? 1 : 0;
     prm->interval_ok = ok;
     if (!ok) atomicOr(flags, 0x100u);
@@ -323,9 +320,7 @@ __global__ void lz_finish_kernel(int k, const double* alpha, const double* beta,
     const double r = fabs(beta[k - 1]) * last;
     const double bnew = theta + fmax(r, 1e-4 * fabs(theta));
     if (isfinite(bnew) && bnew < prm->b && bnew > prm->a) {
-        prm->b = bnew;
-        prm->scale = (float)(2.0 / (prm->b - prm->a));
-        prm->shift = (float)((prm->a + prm->b) / (prm->b - prm->a));
+        set_affine(prm, prm->a, bnew);
     }
     (void)flags;
 }

@@ -62,10 +62,12 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
     const VT* __restrict__ val = static_cast<const VT*>(args.val);
     const uint32_t* __restrict__ vbits = args.vbits;
 
-    float scale = 1.f, shift = 0.f;
+    float scale = 1.f, scale_lo = 0.f, shift = 0.f, shift_lo = 0.f;
     if (EPI == 1) {
-        scale = args.prm->scale;
-        shift = args.prm->shift;
+        scale = args.prm->scale_hi;
+        scale_lo = args.prm->scale_lo;
+        shift = args.prm->shift_hi;
+        shift_lo = args.prm->shift_lo;
     }
 
     float4 tacc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -109,11 +111,13 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
         } else {
             const float4 v = signs4(__ldg(vbits + row * NW + wsel), bsh, mask);
             const float4 own = (PREV == 0) ? v : ldg4(args.own + row * MP + p0);
+            // y = scale * acc - shift * own with the hi/lo constant pairs: the
+            // large terms first, then the small corrections.
             float4 y;
-            y.x = fmaf(scale, acc.x, -shift * own.x);
-            y.y = fmaf(scale, acc.y, -shift * own.y);
-            y.z = fmaf(scale, acc.z, -shift * own.z);
-            y.w = fmaf(scale, acc.w, -shift * own.w);
+            y.x = fmaf(scale, acc.x, -shift * own.x) + fmaf(scale_lo, acc.x, -shift_lo * own.x);
+            y.y = fmaf(scale, acc.y, -shift * own.y) + fmaf(scale_lo, acc.y, -shift_lo * own.y);
+            y.z = fmaf(scale, acc.z, -shift * own.z) + fmaf(scale_lo, acc.z, -shift_lo * own.z);
+            y.w = fmaf(scale, acc.w, -shift * own.w) + fmaf(scale_lo, acc.w, -shift_lo * own.w);
             if (PREV == 0) {
                 res = y;
             } else {
