@@ -157,6 +157,40 @@ CLD_API cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* ro
                                void* workspace_dev, size_t workspace_bytes, void* stream,
                                double* logdet_out, double* stderr_out);
 
+/* Size of the library's built-in device scratch array used by
+ * cld_estimate_static (32 MiB). */
+#define CLD_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* Estimate without any device allocation, for callers that cannot allocate
+ * device memory: code whose device memory is entirely owned by another
+ * allocator (a framework's caching pool that must not be bypassed), code that
+ * runs under a fixed device-memory budget, and latency-critical loops that
+ * must never block in cudaMalloc/cudaFree.  The paper has no counterpart: this
+ * is the same estimate as cld_create_csr + cld_set_interval + cld_estimate
+ * (CLD_SPD only), but its scratch lives in one file-scope __device__ array of
+ * CLD_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until
+ * the process exits.
+ *   rowptr, col, val: the CSR matrix on the device, as in cld_create_csr
+ *   a, b, n, M, seed: as in cld_set_interval / cld_estimate
+ *   stream: cudaStream_t to enqueue on (NULL = legacy default stream)
+ *   logdet_out, stderr_out: host doubles (stderr_out may be NULL)
+ * The needed scratch is d x P x 12 bytes for the three recurrence blocks
+ * (P = M rounded up to a power of two >= 4, at most 128) plus small terms;
+ * requests that do not fit are rejected with CLD_ERR_NOMEM and a message that
+ * gives both sizes.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  The first call on each device looks up the array's device address
+ * on that device (cudaGetSymbolAddress, with that device current); make that
+ * first call before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents (the call clears what must start at zero):
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it.  Synchronises `stream` to return.  Errors: as cld_create_csr,
+ * cld_set_interval, cld_set_workspace (CSR checks) and cld_estimate, plus
+ * CLD_ERR_NOMEM when the request exceeds the array. */
+CLD_API cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t* rowptr,
+                                       const int32_t* col, const void* val, cld_dtype val_dtype,
+                                       double a, double b, int n, int M, uint64_t seed,
+                                       void* stream, double* logdet_out, double* stderr_out);
+
 /* Timing of the dominant kernel.  When on, every cld_estimate records CUDA
  * events on its stream around the general recurrence steps (j >= 2) and
  * cld_last_timing returns their elapsed time and the number of such launches

@@ -38,6 +38,8 @@ SIGNATURES = [
     ("cld_host_workspace_size", _i32, [_i64, _i64, _i32, _i32, _i32, _P(_sz)]),
     ("cld_logdet_csr_host", _i32, [_i64, _i64, _vp, _vp, _vp, _i32, _i32, _f64, _f64, _i32, _i32, _u64,
                                    _vp, _sz, _vp, _P(_f64), _P(_f64)]),
+    ("cld_estimate_static", _i32, [_i64, _i64, _vp, _vp, _vp, _i32, _f64, _f64, _i32, _i32, _u64, _vp,
+                                   _P(_f64), _P(_f64)]),
     ("cld_set_profiling", _i32, [_vp, _i32]),
     ("cld_last_timing", _i32, [_vp, _P(ctypes.c_float), _P(_i32), _P(_i32)]),
     ("cld_launch_config", _i32, [_vp, _i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
@@ -159,6 +161,15 @@ def cld_logdet_csr_host(d, nnz, rowptr_host, col_host, val_host, val_dtype, kind
     g, se = ctypes.c_double(), ctypes.c_double()
     _check(load().cld_logdet_csr_host(d, nnz, _ptr(rowptr_host), _ptr(col_host), _ptr(val_host), val_dtype,
                                       kind, a, b, n, M, seed, _ptr(workspace_dev), workspace_bytes,
+                                      stream or None, ctypes.byref(g), ctypes.byref(se)))
+    return g.value, se.value
+
+
+def cld_estimate_static(d, nnz, rowptr, col, val, val_dtype, a, b, n, M, seed, stream=0):
+    """Estimate with the library's built-in device scratch (no allocation);
+    returns (logdet, stderr)."""
+    g, se = ctypes.c_double(), ctypes.c_double()
+    _check(load().cld_estimate_static(d, nnz, _ptr(rowptr), _ptr(col), _ptr(val), val_dtype, a, b, n, M, seed,
                                       stream or None, ctypes.byref(g), ctypes.byref(se)))
     return g.value, se.value
 

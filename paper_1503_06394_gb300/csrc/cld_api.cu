@@ -42,6 +42,11 @@ static cld_status fail(cld_status st, const char* fmt, ...) {
     return st;
 }
 
+namespace cld {
+// Lets other translation units report through cld_last_error().
+void set_error_message(const char* msg) { g_err = msg; }
+}  // namespace cld
+
 #define CUDA_TRY(expr)                                                                     \
     do {                                                                                   \
         cudaError_t e_ = (expr);                                                           \
