@@ -178,6 +178,47 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def time_estimates(m, n, M, seed, interval, steps, warmup, torch, world):
+    """Warm-up, then `steps` timed estimates (interval + estimate each) with CUDA
+    events on the launching stream.  Returns (ms per step, kernel ms per general
+    step launch, general launches, total launches, last result)."""
+
+    def step():
+        if interval is None:
+            m.auto_interval(0)
+        else:
+            m.set_interval(*interval)
+        return m.estimate(n, M, seed)
+
+    for _ in range(warmup):
+        step()
+    m.set_profiling(True)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    step_ms, step_launches, total_launches, r = 0.0, 0, 0, None
+    for i in range(steps):
+        ev[i][0].record(stream)
+        r = step()
+        ev[i][1].record(stream)
+        ms, sl, tl = m.last_timing()
+        step_ms += ms
+        step_launches += sl
+        total_launches += tl + (2 if interval is None else 1)  # + interval kernels
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    total_ms = float(sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)))
+    if world > 1:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    m.set_profiling(False)
+    return total_ms / steps, step_ms / max(1, step_launches), step_launches, total_launches, r
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -195,61 +236,52 @@ def run_ours(args, rank, world):
     n, M = cfg["n"], cfg["M"]
     seed = cfg["probe_seed"] + rank  # independent replicas on independent probe streams
     m = CsrLogdet(B.rowptr, B.col, stored, dtype=args.dtype)
+    if interval is None:
+        m.auto_interval(0)
+    else:
+        m.set_interval(*interval)
+    variant, _ = m.autotune(n, M)
     m.reserve(n, M)
-
-    def step():
-        if interval is None:
-            m.auto_interval(0)
-        else:
-            m.set_interval(*interval)
-        return m.estimate(n, M, seed)
-
-    for _ in range(args.warmup):
-        step()
-    m.set_profiling(True)
     bg, bmin, nnz_off = algorithmic_bytes_per_step(B, M, s_v)
-    stream = torch.cuda.current_stream()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    step_ms, step_launches, total_launches = 0.0, 0, 0
-    results = []
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            ev[i][0].record(stream)
-            r = step()
-            ev[i][1].record(stream)
-            ms, sl, tl = m.last_timing()
-            step_ms += ms
-            step_launches += sl
-            total_launches += tl + (2 if interval is None else 1)  # + interval kernels
-            results.append(r)
-        torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    total_ms = float(sum(per))
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
-    ms_per_step = total_ms / args.steps
-    value = world * n * bg / (ms_per_step / 1e3) / 1e9
     peak, peak_src = read_peaks()
-    kernel_avg_ms = step_ms / max(1, step_launches)
+    with ClockSampler(local) as clk:
+        ms_per_step, kernel_avg_ms, step_launches, total_launches, r_last = time_estimates(
+            m, n, M, seed, interval, args.steps, args.warmup, torch, world)
+    value = world * n * bg / (ms_per_step / 1e3) / 1e9
     achieved = bg / (kernel_avg_ms / 1e3) / 1e9
     panel, lpr, ctas, threads = m.launch_config(M)
+    a_e, b_e = (interval if interval is not None else Bd.cld_auto_interval(m.h, 0))
+    rr = m.estimate(n, M, cfg["probe_seed"], details=True)
+    gp0_ours = float(rr["gamma_p"][0])
+    m.close()
+    del m
+    torch.cuda.empty_cache()
+
+    # BF16-stored values on the same GPU (FP32 recurrence vectors)
+    bf16 = None
+    if args.dtype == "f32" and not args.no_bf16:
+        st16, v16 = B.stored("bf16")
+        m16 = CsrLogdet(B.rowptr, B.col, st16, dtype="bf16")
+        iv16 = interval
+        if iv16 is None:
+            iv16 = m16.auto_interval(0)
+        m16.autotune(n, M)
+        bg16, _, _ = algorithmic_bytes_per_step(B, M, 2)
+        ms16, k16, _, _, _ = time_estimates(m16, n, M, seed, interval, args.steps, max(1, args.warmup - 1), torch, world)
+        m16.set_interval(*iv16)
+        r16 = m16.estimate(n, M, cfg["probe_seed"], details=True)
+        bf16 = {"value": world * n * bg16 / (ms16 / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms16,
+                "kernel_ms": k16, "logdet": r16["logdet"], "gamma_p0": float(r16["gamma_p"][0]),
+                "vs_fp32_time": ms16 / ms_per_step}
+        m16.close()
+        del m16
+        torch.cuda.empty_cache()
 
     # end to end through the host-buffer entry point (pinned host arrays)
     rp = torch.from_numpy(B.rowptr).pin_memory()
     cl = torch.from_numpy(B.col).pin_memory()
     vv = torch.from_numpy(stored.view(np.int16) if args.dtype == "bf16" else stored).pin_memory()
-    a_e, b_e = (interval if interval is not None else Bd.cld_auto_interval(m.h, 0))
     need = Bd.cld_host_workspace_size(B.d, B.nnz, {"f32": 0, "bf16": 1, "f64": 2}[args.dtype], n, M)
-    m.close()
-    del m
-    torch.cuda.empty_cache()
     ws = torch.empty(need, dtype=torch.uint8, device="cuda")
     logdet_host(rp, cl, vv, a_e, b_e, n, M, seed, dtype=args.dtype, workspace=ws)
     torch.cuda.synchronize()
@@ -274,37 +306,59 @@ def run_ours(args, rank, world):
                        if B.d * panel * 4 > 2e8 else "L2-resident workload (no flush)",
                        "interval": "gershgorin on device each step" if interval is None else "closed form %s" % (interval,),
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "launch": {"panel": panel, "lanes_per_row": lpr, "ctas": ctas, "threads": threads}},
-            "logdet": results[-1]["logdet"], "stderr": results[-1]["stderr"],
+                       "launch": {"panel": panel, "lanes_per_row": lpr, "ctas": ctas, "threads": threads,
+                                  "variant": variant}},
+            "logdet": r_last["logdet"], "stderr": r_last["stderr"],
             "logdet_s": ms_per_step / 1e3, "pct_of_peak": 100.0 * value / world / peak,
             "b_gather_per_step": bg, "b_min_per_step": bmin,
             "effective_gbs_bmin": world * n * bmin / (ms_per_step / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": profiled_traffic(args, B),
                          "kernel": "step_kernel (general recurrence step, j >= 2)",
                          "avg_launch_ms": kernel_avg_ms, "peak_source": peak_src},
             "gpu_launches": total_launches,
             "e2e": {"value": world * n * bg / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 32, "seconds_per_step": e2e_s},
             "clocks": clk.summary(), "generation_s": gen_s}
+    if bf16 is not None:
+        line["bf16"] = bf16
     if not args.no_cpu_baseline:
+        # the oracle on the original FP64 values, probe 0: the CPU baseline and
+        # the reference for the relative errors of the FP32 and BF16 results
         a_c, b_c = (interval if interval is not None else (a_e, b_e))
-        dt, steps, probes, t_cpu, threads = cpu_sample(B, v64, a_c, b_c, n, M, budget_s=args.cpu_budget)
+        dt, steps, probes, t_cpu, threads = cpu_sample(B, B.val, a_c, b_c, n, M, budget_s=args.cpu_budget)
         bg1, _, _ = algorithmic_bytes_per_step(B, 1, s_v)
         line["cpu_baseline"] = {"value": steps * bg1 / dt / 1e9, "unit": "GB/s", "cores": threads,
                                 "kind": "oracle",
                                 "sample": "probe 0 of %d, %d of %d degree steps, full d=%d, FP64" % (M, steps, n, B.d)}
         if t_cpu is not None:
-            # parity of the timed run's probe 0 against the oracle (same probes, same interval)
-            mm = CsrLogdet(B.rowptr, B.col, stored, dtype=args.dtype)
-            mm.set_interval(a_c, b_c)
-            rr = mm.estimate(n, M, cfg["probe_seed"], moments=True, details=True)
             import oracle
 
-            gp0 = float(np.dot(rr["c"], t_cpu[:, 0]))
-            line["rel_err_probe0_vs_oracle"] = abs(rr["gamma_p"][0] - gp0) / abs(gp0)
-            mm.close()
+            gp0 = float(np.dot(oracle.cheb_coeffs(n, a_c, b_c), t_cpu[:, 0]))
+            line["rel_err_probe0_vs_fp64_oracle"] = abs(gp0_ours - gp0) / abs(gp0)
+            if bf16 is not None:
+                bf16["rel_err_probe0_vs_fp64_oracle"] = abs(bf16["gamma_p0"] - gp0) / abs(gp0)
     print(json.dumps(line), flush=True)
+
+
+def profiled_traffic(args, B):
+    """DRAM bytes (read + write) per general-step launch from the committed ncu
+    summary of this workload, if the step kernel's source is unchanged since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "step_kernel_config2_traffic.md")
+    src = os.path.join(ROOT, "paper_1503_06394_gb300", "csrc", "step_kernel.cuh")
+    if args.config != 2 or args.d or args.dtype != "f32" or not os.path.exists(path):
+        return None
+    text = open(path).read()
+    want = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())
+    if vals.get("step_kernel_sha256", "").strip() != want:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"].strip())
+    except (KeyError, ValueError):
+        return None
 
 
 def main():
@@ -318,6 +372,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--d", type=int, default=None, help="override the dimension (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage measurement")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

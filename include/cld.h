@@ -191,6 +191,25 @@ CLD_API cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t* ro
                                        double a, double b, int n, int M, uint64_t seed,
                                        void* stream, double* logdet_out, double* stderr_out);
 
+/* Selects the inner loop of the recurrence-step kernel (a tuning control; all
+ * variants compute the same sums in the same order):
+ *   0: each lane loads 4 (column, value) pairs itself, 4 row gathers in flight;
+ *   1: the lanes of a row load 8 pairs cooperatively and issue 8 row gathers
+ *      back to back, the next chunk's pairs loaded ahead (default);
+ *   2: as 1 with chunks of 4 pairs (fewer registers, more resident CTAs).
+ * The default at creation is 2 when the matrix holds >= 8 stored entries per
+ * row on average, else 0.  The variant also sets the grid size, so the last
+ * bits of the moments (their summation order) can change with it.
+ * Errors: CLD_ERR_INVALID for an unknown variant. */
+CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
+
+/* Autotuner: times `reps` launches of the general recurrence step of every
+ * variant on this matrix with M probes (workspace and interval must be set;
+ * the workspace contents are overwritten) and keeps the fastest on the handle.
+ * Returns the chosen variant and its mean step time in ms (either may be NULL).
+ * Errors: CLD_ERR_INVALID, CLD_ERR_NOMEM, CLD_ERR_INTERVAL, CLD_ERR_CUDA. */
+CLD_API cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* ms_out);
+
 /* Timing of the dominant kernel.  When on, every cld_estimate records CUDA
  * events on its stream around the general recurrence steps (j >= 2) and
  * cld_last_timing returns their elapsed time and the number of such launches

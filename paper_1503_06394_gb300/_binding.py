@@ -40,6 +40,8 @@ SIGNATURES = [
                                    _vp, _sz, _vp, _P(_f64), _P(_f64)]),
     ("cld_estimate_static", _i32, [_i64, _i64, _vp, _vp, _vp, _i32, _f64, _f64, _i32, _i32, _u64, _vp,
                                    _P(_f64), _P(_f64)]),
+    ("cld_set_kernel_variant", _i32, [_vp, _i32]),
+    ("cld_autotune", _i32, [_vp, _i32, _i32, _P(_i32), _P(ctypes.c_float)]),
     ("cld_set_profiling", _i32, [_vp, _i32]),
     ("cld_last_timing", _i32, [_vp, _P(ctypes.c_float), _P(_i32), _P(_i32)]),
     ("cld_launch_config", _i32, [_vp, _i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
@@ -172,6 +174,18 @@ def cld_estimate_static(d, nnz, rowptr, col, val, val_dtype, a, b, n, M, seed, s
     _check(load().cld_estimate_static(d, nnz, _ptr(rowptr), _ptr(col), _ptr(val), val_dtype, a, b, n, M, seed,
                                       stream or None, ctypes.byref(g), ctypes.byref(se)))
     return g.value, se.value
+
+
+def cld_set_kernel_variant(h, variant):
+    _check(load().cld_set_kernel_variant(h, variant))
+
+
+def cld_autotune(h, M, reps=3):
+    """Times every step-kernel variant on this matrix and keeps the fastest;
+    returns (variant, ms per step)."""
+    v, ms = ctypes.c_int(), ctypes.c_float()
+    _check(load().cld_autotune(h, M, reps, ctypes.byref(v), ctypes.byref(ms)))
+    return v.value, ms.value
 
 
 def cld_set_profiling(h, on):

@@ -89,6 +89,15 @@ class CsrLogdet:
             out["c"], out["gamma_p"] = B.cld_last_details(self.h, n, M)
         return out
 
+    def set_kernel_variant(self, variant: int):
+        B.cld_set_kernel_variant(self.h, variant)
+
+    def autotune(self, n: int, M: int, reps: int = 3):
+        """Picks the fastest recurrence-step variant for this matrix (n, M
+        size the workspace)."""
+        self.reserve(n, M)
+        return B.cld_autotune(self.h, M, reps)
+
     def set_profiling(self, on: bool = True):
         B.cld_set_profiling(self.h, on)
 

@@ -10,9 +10,9 @@ namespace cld {
 cudaError_t launch_step_f32(int panel, StepKind kind, int grid, cudaStream_t s, const StepArgs& a);
 cudaError_t launch_step_bf16(int panel, StepKind kind, int grid, cudaStream_t s, const StepArgs& a);
 cudaError_t launch_step_f64(int panel, StepKind kind, int grid, cudaStream_t s, const StepArgs& a);
-int step_ctas_per_sm_f32(int panel);
-int step_ctas_per_sm_bf16(int panel);
-int step_ctas_per_sm_f64(int panel);
+int step_ctas_per_sm_f32(int panel, int impl);
+int step_ctas_per_sm_bf16(int panel, int impl);
+int step_ctas_per_sm_f64(int panel, int impl);
 
 cudaError_t launch_step(int panel, int dtype, StepKind kind, int grid, cudaStream_t stream,
                         const StepArgs& a) {
@@ -24,11 +24,11 @@ cudaError_t launch_step(int panel, int dtype, StepKind kind, int grid, cudaStrea
     }
 }
 
-int step_ctas_per_sm(int panel, int dtype) {
+int step_ctas_per_sm(int panel, int dtype, int impl) {
     switch (dtype) {
-        case 0: return step_ctas_per_sm_f32(panel);
-        case 1: return step_ctas_per_sm_bf16(panel);
-        case 2: return step_ctas_per_sm_f64(panel);
+        case 0: return step_ctas_per_sm_f32(panel, impl);
+        case 1: return step_ctas_per_sm_bf16(panel, impl);
+        case 2: return step_ctas_per_sm_f64(panel, impl);
         default: return 1;
     }
 }

@@ -91,6 +91,12 @@ __device__ __forceinline__ float load_val(const bf16_t* p) {
     uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(p));
     return __uint_as_float(((uint32_t)b) << 16);
 }
+__device__ __forceinline__ float load_val_cs(const float* p) { return __ldcs(p); }
+__device__ __forceinline__ float load_val_cs(const double* p) { return (float)__ldcs(p); }
+__device__ __forceinline__ float load_val_cs(const bf16_t* p) {
+    uint16_t b = __ldcs(reinterpret_cast<const unsigned short*>(p));
+    return __uint_as_float(((uint32_t)b) << 16);
+}
 __device__ __forceinline__ double load_val_f64(const float* p) { return (double)__ldg(p); }
 __device__ __forceinline__ double load_val_f64(const double* p) { return __ldg(p); }
 __device__ __forceinline__ double load_val_f64(const bf16_t* p) {
@@ -119,7 +125,10 @@ struct StepArgs {
     double* tpart;           // [grid][panel] partial moments (epi 1)
     const Params* prm;
     int mreal;               // real probes in this panel
+    int impl;                // inner-loop variant (0 or 1, see step_kernel.cuh)
 };
+
+constexpr int kNumStepImpls = 3;
 
 enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
                 kStepFirstFromFloat = 5 };
@@ -128,7 +137,7 @@ enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3
 cudaError_t launch_step(int panel, int dtype, StepKind kind, int grid, cudaStream_t stream,
                         const StepArgs& a);
 // Resident CTAs per SM of the general step kernel (for grid sizing).
-int step_ctas_per_sm(int panel, int dtype);
+int step_ctas_per_sm(int panel, int dtype, int impl);
 // Number of sign words per row for a panel width.
 inline int sign_words(int panel) { return panel <= 32 ? 1 : panel / 32; }
 

@@ -101,7 +101,7 @@ extern "C" cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t*
     const int nw = sign_words(panel);
     const int rows_per_cta = (kThreads / 32) * (128 / panel);
     int64_t g = (d + rows_per_cta - 1) / rows_per_cta;
-    const int64_t gfull = (int64_t)step_ctas_per_sm(panel, (int)val_dtype) * sms;
+    const int64_t gfull = (int64_t)step_ctas_per_sm(panel, (int)val_dtype, 0) * sms;
     const int grid = (int)(g < gfull ? (g > 0 ? g : 1) : gfull);
     int64_t sg = (d + kThreads - 1) / kThreads;
     const int sgrid = (int)(sg < (int64_t)sms * 8 ? (sg > 0 ? sg : 1) : (int64_t)sms * 8);

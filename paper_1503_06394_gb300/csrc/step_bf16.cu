@@ -8,6 +8,6 @@ cudaError_t launch_step_bf16(int panel, StepKind kind, int grid, cudaStream_t s,
     return launch_step_vt<bf16_t>(panel, kind, grid, s, a);
 }
 
-int step_ctas_per_sm_bf16(int panel) { return ctas_per_sm_vt<bf16_t>(panel); }
+int step_ctas_per_sm_bf16(int panel, int impl) { return ctas_per_sm_vt<bf16_t>(panel, impl); }
 
 }  // namespace cld

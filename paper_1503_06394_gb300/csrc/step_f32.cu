@@ -8,6 +8,6 @@ cudaError_t launch_step_f32(int panel, StepKind kind, int grid, cudaStream_t s, 
     return launch_step_vt<float>(panel, kind, grid, s, a);
 }
 
-int step_ctas_per_sm_f32(int panel) { return ctas_per_sm_vt<float>(panel); }
+int step_ctas_per_sm_f32(int panel, int impl) { return ctas_per_sm_vt<float>(panel, impl); }
 
 }  // namespace cld

@@ -8,6 +8,6 @@ cudaError_t launch_step_f64(int panel, StepKind kind, int grid, cudaStream_t s, 
     return launch_step_vt<double>(panel, kind, grid, s, a);
 }
 
-int step_ctas_per_sm_f64(int panel) { return ctas_per_sm_vt<double>(panel); }
+int step_ctas_per_sm_f64(int panel, int impl) { return ctas_per_sm_vt<double>(panel, impl); }
 
 }  // namespace cld

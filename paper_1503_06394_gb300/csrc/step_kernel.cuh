@@ -33,9 +33,113 @@ __device__ __forceinline__ float4 ldcs4(const float* p) {
 }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
+// Row product acc = sum_k X[row, k] * x[k, p0..p0+3] over the stored entries
+// [k0, k1) of one row, for the four probes of this lane.
+//
+// IMPL 0: each lane loads the column index and value of 4 entries at a time
+//         itself, then gathers those 4 rows (4 gathers in flight per group).
+// IMPL 1 (2): the LPR lanes of the group load the next 8 (4) (index, value) pairs
+//         cooperatively (one coalesced access per lane), broadcast them with
+//         shuffles and issue all 8 (4) row gathers back to back; the indices of the
+//         following chunk are loaded before the current chunk's gathers are
+//         consumed.  CSR streams are read with the evict-first policy so they
+//         do not displace gathered rows of w_j from L2.
+//
+// The shuffles of IMPL 1/2 name only the LPR lanes of the row's group
+// (gmask): groups of one warp own rows of different lengths, so their chunk
+// loops (and the last grid-stride round) diverge, and a full-warp mask would be
+// undefined there.
+template <int MP, int GATHER, int IMPL, typename VT>
+__device__ __forceinline__ float4 row_product(int64_t k0, int64_t k1, const int32_t* __restrict__ col,
+                                              const VT* __restrict__ val, const float* __restrict__ x,
+                                              const uint32_t* __restrict__ vbits, int lig, int p0,
+                                              int wsel, int bsh, float4 mask, unsigned gmask) {
+    constexpr int LPR = MP / 4;
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (IMPL == 0) {
+        constexpr int U = 4;
+        for (int64_t k = k0; k < k1; k += U) {
+            int c[U];
+            float a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = k + u < k1;
+                c[u] = ok ? __ldg(col + k + u) : -1;
+                a[u] = ok ? load_val(val + k + u) : 0.f;
+            }
+            float4 xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] >= 0) {
+                    if (GATHER == 1)
+                        xv[u] = signs4(__ldg(vbits + (int64_t)c[u] * NW + wsel), bsh, mask);
+                    else
+                        xv[u] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)c[u] * MP + p0));
+                } else {
+                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc.x = fmaf(a[u], xv[u].x, acc.x);
+                acc.y = fmaf(a[u], xv[u].y, acc.y);
+                acc.z = fmaf(a[u], xv[u].z, acc.z);
+                acc.w = fmaf(a[u], xv[u].w, acc.w);
+            }
+        }
+    } else {
+        constexpr int CH = IMPL == 1 ? 8 : 4;        // entries per chunk
+        constexpr int E = LPR >= CH ? 1 : CH / LPR;  // entries held per lane
+        int creg[E], cnext[E];
+        float vreg[E], vnext[E];
+        auto load_chunk = [&](int64_t kb, int* cr, float* vr) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int idx = e * LPR + lig;  // entry of the chunk this lane loads
+                const int64_t k = kb + idx;
+                const bool ok = idx < CH && k < k1;
+                cr[e] = ok ? __ldcs(col + k) : 0;
+                vr[e] = ok ? load_val_cs(val + k) : 0.f;
+            }
+        };
+        load_chunk(k0, creg, vreg);
+        for (int64_t k = k0; k < k1; k += CH) {
+            if (k + CH < k1) load_chunk(k + CH, cnext, vnext);
+            float4 xv[CH];
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const int c = __shfl_sync(gmask, creg[u / LPR], u % LPR, LPR);
+                if (k + u < k1) {
+                    if (GATHER == 1)
+                        xv[u] = signs4(__ldg(vbits + (int64_t)c * NW + wsel), bsh, mask);
+                    else
+                        xv[u] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)c * MP + p0));
+                } else {
+                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < CH; ++u) {
+                const float av = __shfl_sync(gmask, vreg[u / LPR], u % LPR, LPR);
+                acc.x = fmaf(av, xv[u].x, acc.x);
+                acc.y = fmaf(av, xv[u].y, acc.y);
+                acc.z = fmaf(av, xv[u].z, acc.z);
+                acc.w = fmaf(av, xv[u].w, acc.w);
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                creg[e] = cnext[e];
+                vreg[e] = vnext[e];
+            }
+        }
+    }
+    return acc;
+}
+
 // GATHER: 0 float rows of args.x, 1 probe signs.  PREV: 0 none, 1 v, 2 args.wprev.
-// EPI: 0 plain product, 1 recurrence + moments.
-template <int MP, typename VT, int GATHER, int PREV, int EPI>
+// EPI: 0 plain product, 1 recurrence + moments.  IMPL: inner loop (row_product).
+template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
 __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
     constexpr int LPR = MP / 4;          // lanes per row
     constexpr int GPW = 32 / LPR;        // rows per warp
@@ -72,38 +176,28 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
 
     float4 tacc = make_float4(0.f, 0.f, 0.f, 0.f);
 
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g_in_w * LPR));
+    int64_t k0 = 0, k1 = 0;
+    if (IMPL != 0 && gid < d) {
+        k0 = __ldg(rowptr + gid);
+        k1 = __ldg(rowptr + gid + 1);
+    }
     for (int64_t row = gid; row < d; row += ngroups) {
-        const int64_t k0 = __ldg(rowptr + row);
-        const int64_t k1 = __ldg(rowptr + row + 1);
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t k = k0; k < k1; k += U) {
-            int c[U];
-            float a[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = k + u < k1;
-                c[u] = ok ? __ldg(col + k + u) : -1;
-                a[u] = ok ? load_val(val + k + u) : 0.f;
+        float4 acc;
+        if (IMPL == 0) {
+            k0 = __ldg(rowptr + row);
+            k1 = __ldg(rowptr + row + 1);
+            acc = row_product<MP, GATHER, IMPL>(k0, k1, col, val, args.x, vbits, lig, p0, wsel, bsh, mask, gmask);
+        } else {
+            // row pointers of this group's next row, loaded ahead
+            int64_t n0 = 0, n1 = 0;
+            if (row + ngroups < d) {
+                n0 = __ldg(rowptr + row + ngroups);
+                n1 = __ldg(rowptr + row + ngroups + 1);
             }
-            float4 xv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (c[u] >= 0) {
-                    if (GATHER == 1)
-                        xv[u] = signs4(__ldg(vbits + (int64_t)c[u] * NW + wsel), bsh, mask);
-                    else
-                        xv[u] = ldg4(args.x + (int64_t)c[u] * MP + p0);
-                } else {
-                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                acc.x = fmaf(a[u], xv[u].x, acc.x);
-                acc.y = fmaf(a[u], xv[u].y, acc.y);
-                acc.z = fmaf(a[u], xv[u].z, acc.z);
-                acc.w = fmaf(a[u], xv[u].w, acc.w);
-            }
+            acc = row_product<MP, GATHER, IMPL>(k0, k1, col, val, args.x, vbits, lig, p0, wsel, bsh, mask, gmask);
+            k0 = n0;
+            k1 = n1;
         }
         float4 res;
         if (EPI == 0) {
@@ -161,18 +255,28 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
     }
 }
 
-template <int MP, typename VT>
-cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
+template <int MP, typename VT, int IMPL>
+cudaError_t launch_step_impl(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
     switch (kind) {
-        case kStepFirst: step_kernel<MP, VT, 1, 0, 1><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepSecond: step_kernel<MP, VT, 0, 1, 1><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepGeneral: step_kernel<MP, VT, 0, 2, 1><<<grid, kThreads, 0, s>>>(a); break;
-        case kProdBits: step_kernel<MP, VT, 1, 0, 0><<<grid, kThreads, 0, s>>>(a); break;
-        case kProdFloat: step_kernel<MP, VT, 0, 0, 0><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepFirstFromFloat: step_kernel<MP, VT, 0, 0, 1><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepFirst: step_kernel<MP, VT, 1, 0, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepSecond: step_kernel<MP, VT, 0, 1, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepGeneral: step_kernel<MP, VT, 0, 2, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kProdBits: step_kernel<MP, VT, 1, 0, 0, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kProdFloat: step_kernel<MP, VT, 0, 0, 0, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepFirstFromFloat: step_kernel<MP, VT, 0, 0, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+template <int MP, typename VT>
+cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
+    switch (a.impl) {
+        case 0: return launch_step_impl<MP, VT, 0>(kind, grid, s, a);
+        case 1: return launch_step_impl<MP, VT, 1>(kind, grid, s, a);
+        case 2: return launch_step_impl<MP, VT, 2>(kind, grid, s, a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename VT>
@@ -189,23 +293,26 @@ cudaError_t launch_step_vt(int panel, StepKind kind, int grid, cudaStream_t s, c
 }
 
 template <int MP, typename VT>
-int ctas_per_sm_mp() {
+int ctas_per_sm_mp(int impl) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1>, kThreads, 0) !=
-        cudaSuccess)
-        return 1;
+    cudaError_t e = impl == 0
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1, 0>, kThreads, 0)
+        : impl == 1
+        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1, 1>, kThreads, 0)
+        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1, 2>, kThreads, 0);
+    if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 
 template <typename VT>
-int ctas_per_sm_vt(int panel) {
+int ctas_per_sm_vt(int panel, int impl) {
     switch (panel) {
-        case 4: return ctas_per_sm_mp<4, VT>();
-        case 8: return ctas_per_sm_mp<8, VT>();
-        case 16: return ctas_per_sm_mp<16, VT>();
-        case 32: return ctas_per_sm_mp<32, VT>();
-        case 64: return ctas_per_sm_mp<64, VT>();
-        case 128: return ctas_per_sm_mp<128, VT>();
+        case 4: return ctas_per_sm_mp<4, VT>(impl);
+        case 8: return ctas_per_sm_mp<8, VT>(impl);
+        case 16: return ctas_per_sm_mp<16, VT>(impl);
+        case 32: return ctas_per_sm_mp<32, VT>(impl);
+        case 64: return ctas_per_sm_mp<64, VT>(impl);
+        case 128: return ctas_per_sm_mp<128, VT>(impl);
         default: return 1;
     }
 }

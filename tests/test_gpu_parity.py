@@ -17,23 +17,25 @@ def torch():
     return require_gpu()
 
 
-def run_gpu(B, dtype, a, b, n, M, seed=0, moments=True):
+def run_gpu(B, dtype, a, b, n, M, seed=0, moments=True, variant=None):
     from paper_1503_06394_gb300 import CsrLogdet
 
     stored, _ = B.stored(dtype)
     m = CsrLogdet(B.rowptr, B.col, stored, dtype=dtype)
+    if variant is not None:
+        m.set_kernel_variant(variant)
     m.set_interval(a, b)
     r = m.estimate(n, M, seed, moments=moments, details=True)
     m.close()
     return r
 
 
-def check(B, dtype, n, M, seed=0, probes=None, interval=None, tol_gamma=1e-5, structured=False):
+def check(B, dtype, n, M, seed=0, probes=None, interval=None, tol_gamma=1e-5, structured=False, variant=None):
     _, v64 = B.stored(dtype)
     a, b = interval if interval is not None else oracle.gershgorin(B.rowptr, B.col, v64)
     if not b - a > 1e-9 * abs(b):  # one-point spectrum (d = 1): widen
         a, b = 0.5 * a, 1.5 * b
-    r = run_gpu(B, dtype, a, b, n, M, seed)
+    r = run_gpu(B, dtype, a, b, n, M, seed, variant=variant)
     ref = oracle.estimate(B.rowptr, B.col, v64, a, b, n, M, seed=seed, probes=probes)
     cols = np.arange(M) if probes is None else np.asarray(probes)
     dt = np.abs(r["t"][:, cols] - ref["t"])
@@ -51,6 +53,32 @@ def check(B, dtype, n, M, seed=0, probes=None, interval=None, tol_gamma=1e-5, st
 def test_parity_shapes(torch, d, M):
     B = workloads.sparse_random_spd(d, 3, 100 + d)
     check(B, "f32", 12, M, seed=d + M)
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("M", [3, 8, 16, 32, 64, 128])
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_parity_kernel_variants(torch, variant, M, dtype):
+    """Every inner-loop variant at every panel width (4..128 probes), on rows of
+    1 to ~50 entries, including a final grid-stride round that only some row
+    groups of a warp take."""
+    rng = np.random.default_rng(M)
+    d = 4099
+    deg = rng.integers(0, 25, size=d)
+    rows = np.repeat(np.arange(d), deg)
+    cols = rng.integers(0, d, size=rows.size)
+    keep = rows != cols
+    Bo = workloads._coo_to_csr(d, rows[keep], cols[keep], rng.standard_normal(int(keep.sum())), "v")
+    B = workloads._with_diagonal(d, Bo, np.zeros(d), "v")
+    A = workloads.Csr(B.rowptr, B.col, B.val)
+    # symmetrise: (A + A^T) with a dominant diagonal
+    sym = workloads._coo_to_csr(d, np.concatenate([np.repeat(np.arange(d), np.diff(A.rowptr)), A.col]),
+                                np.concatenate([A.col, np.repeat(np.arange(d), np.diff(A.rowptr))]),
+                                np.concatenate([A.val, A.val]), "sym")
+    rs = workloads._abs_row_sums(d, sym)
+    S = workloads._with_diagonal(d, sym, rs + 1.0, "sym")
+    S.val = S.val / (2 * rs.max() + 1.0)
+    check(S, dtype, 9, M, seed=M + variant, variant=variant)
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3])
@@ -232,4 +260,20 @@ def test_profiling_counts_launches(torch):
     m.estimate(20, 32, 0)
     ms, steps, total = m.last_timing()
     assert ms > 0 and steps == 18 and total == 20 + 4
+    m.close()
+
+
+def test_autotune_keeps_parity(torch):
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    B = workloads.sparse_random_spd(30000, 5, 77)
+    v32, v64 = B.stored("f32")
+    lo, hi = oracle.gershgorin(B.rowptr, B.col, v64)
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    m.set_interval(lo, hi)
+    variant, ms = m.autotune(20, 32)
+    assert variant in (0, 1, 2) and ms > 0
+    r = m.estimate(20, 32, 1)
+    ref = oracle.estimate(B.rowptr, B.col, v64, lo, hi, 20, 32, seed=1)
+    assert abs(r["logdet"] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
     m.close()
