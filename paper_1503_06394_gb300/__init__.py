@@ -10,8 +10,17 @@ thin Python binding:
   point, same names (``cld_create_csr``, ``cld_estimate``, ...);
 * ``CsrLogdet`` / ``logdet`` -- convenience wrappers that hold the device
   arrays and the workspace as torch tensors (PyTorch supplies device memory
-  and streams only).
+  and streams only);
+* ``autograd.CldLogdet`` -- a torch.autograd.Function whose backward is the
+  library's adjoint kernel (cld_grad).
 """
 from ._binding import *  # noqa: F401,F403
 from ._binding import CldError, load  # noqa: F401
 from .api import CsrLogdet, logdet, logdet_host  # noqa: F401
+
+
+def autograd_logdet(values, rowptr, col, n, M, seed=0, interval=(None, None)):
+    """torch.autograd-aware estimate (see autograd.py); imports torch lazily."""
+    from .autograd import logdet as _ad
+
+    return _ad(values, rowptr, col, n, M, seed, interval)

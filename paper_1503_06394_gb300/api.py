@@ -89,6 +89,14 @@ class CsrLogdet:
             out["c"], out["gamma_p"] = B.cld_last_details(self.h, n, M)
         return out
 
+    def grad(self, n: int, M: int, seed: int = 0):
+        """(logdet, dGamma/dval as an FP32 CUDA tensor of nnz entries); the
+        interval is held fixed.  Needs a structurally symmetric pattern."""
+        self.reserve(n, M, 1)
+        G = self.torch.empty(self.nnz, dtype=self.torch.float32, device=self.device)
+        g = B.cld_grad(self.h, n, M, seed, G)
+        return g, G
+
     def set_kernel_variant(self, variant: int):
         B.cld_set_kernel_variant(self.h, variant)
 

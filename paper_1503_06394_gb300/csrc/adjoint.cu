@@ -1,0 +1,171 @@
+// Adjoint (reverse-mode gradient) of the Chebyshev-Hutchinson estimate with
+// respect to the stored values of a symmetric B, the interval [a, b] held fixed.
+// The paper has no gradient; this differentiates the recurrence of Sec. 2.2.
+//
+// With At = scale B - shift I (scale = 2/(b-a), shift = (a+b)/(b-a)),
+// w_0 = v, w_1 = At v, w_{j+1} = 2 At w_j - w_{j-1} and
+// Gamma_p = sum_j c_j v^T w_j, the adjoint vectors
+//   lambda_{n+1} = lambda_{n+2} = 0,
+//   lambda_i = c_i v + 2 At lambda_{i+1} - lambda_{i+2}   (i = n .. 1)
+// give, for a stored entry (r, k),
+//   dGamma_p / dB_rk = scale * (lambda_1[r] v[k] + 2 sum_{i=1}^{n-1} lambda_{i+1}[r] w_i[k]).
+//
+// Fused SDDMM: the pass that forms lambda_i over row k gathers lambda_{i+1}[r]
+// for every stored (k, r) and holds w_i[k]; for a symmetric pattern that is the
+// term of entry (r, k), so it is accumulated at the position of (k, r) in H and
+// mapped through the transpose at the end (no extra gathers).
+#include <math.h>
+
+#include "cld_internal.cuh"
+
+namespace cld {
+
+
+
+// MODE 0: lambda_{i+1} = 0 (i = n): lambda_i = c_i v; no gather, no H term.
+// MODE 1: lambda_{i+2} = 0 (i = n - 1).
+// MODE 2: general.
+// MODE 3: final pass: H[pos(k,r)] += sum_p lambda_in[r,p] v[k,p]; no lambda_out.
+template <int MP, typename VT, int MODE>
+__global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs args) {
+    constexpr int LPR = MP / 4;
+    constexpr int GPW = 32 / LPR;
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    constexpr int WPB = kThreads / 32;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int lig = lane % LPR;
+    const int g_in_w = lane / LPR;
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g_in_w * LPR));
+    const int64_t gid = ((int64_t)blockIdx.x * WPB + warp) * GPW + g_in_w;
+    const int64_t ngroups = (int64_t)gridDim.x * WPB * GPW;
+    const int p0 = 4 * lig, wsel = p0 >> 5, bsh = p0 & 31;
+    const float4 mask = make_float4(p0 < args.mreal ? 1.f : 0.f, p0 + 1 < args.mreal ? 1.f : 0.f,
+                                    p0 + 2 < args.mreal ? 1.f : 0.f, p0 + 3 < args.mreal ? 1.f : 0.f);
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
+    const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
+    const float ci = MODE == 3 ? 0.f : (float)args.coeffs[args.ci];
+    const float hfac = MODE == 3 ? 1.f : 2.f;
+
+    for (int64_t row = gid; row < args.d; row += ngroups) {
+        const float4 v = signs4(__ldg(args.vbits + row * NW + wsel), bsh, mask);
+        if (MODE == 0) {
+            *reinterpret_cast<float4*>(args.lam_out + row * MP + p0) =
+                make_float4(ci * v.x, ci * v.y, ci * v.z, ci * v.w);
+            continue;
+        }
+        const float4 wk = MODE == 3 ? v : __ldg(reinterpret_cast<const float4*>(args.w + row * MP + p0));
+        const int64_t k0 = __ldg(args.rowptr + row), k1 = __ldg(args.rowptr + row + 1);
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int64_t k = k0; k < k1; k += U) {
+            int c[U];
+            float a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = k + u < k1;
+                c[u] = ok ? __ldg(args.col + k + u) : -1;
+                a[u] = ok ? load_val(val + k + u) : 0.f;
+            }
+            float4 xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                xv[u] = c[u] >= 0 ? __ldg(reinterpret_cast<const float4*>(args.lam_in + (int64_t)c[u] * MP + p0))
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                acc.x = fmaf(a[u], xv[u].x, acc.x);
+                acc.y = fmaf(a[u], xv[u].y, acc.y);
+                acc.z = fmaf(a[u], xv[u].z, acc.z);
+                acc.w = fmaf(a[u], xv[u].w, acc.w);
+                float dt = xv[u].x * wk.x;
+                dt = fmaf(xv[u].y, wk.y, dt);
+                dt = fmaf(xv[u].z, wk.z, dt);
+                dt = fmaf(xv[u].w, wk.w, dt);
+#pragma unroll
+                for (int off = LPR / 2; off >= 1; off >>= 1) dt += __shfl_xor_sync(gmask, dt, off, LPR);
+                if (lig == 0 && c[u] >= 0) args.H[k + u] = fmaf(hfac, dt, args.H[k + u]);
+            }
+        }
+        if (MODE == 3) continue;
+        const float4 own = __ldg(reinterpret_cast<const float4*>(args.lam_in + row * MP + p0));
+        float4 y;
+        y.x = fmaf(scale, acc.x, -shift * own.x) + fmaf(scale_lo, acc.x, -shift_lo * own.x);
+        y.y = fmaf(scale, acc.y, -shift * own.y) + fmaf(scale_lo, acc.y, -shift_lo * own.y);
+        y.z = fmaf(scale, acc.z, -shift * own.z) + fmaf(scale_lo, acc.z, -shift_lo * own.z);
+        y.w = fmaf(scale, acc.w, -shift * own.w) + fmaf(scale_lo, acc.w, -shift_lo * own.w);
+        float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (MODE == 2) pv = __ldcs(reinterpret_cast<const float4*>(args.lam_prev + row * MP + p0));
+        float4 out;
+        out.x = fmaf(ci, v.x, fmaf(2.f, y.x, -pv.x));
+        out.y = fmaf(ci, v.y, fmaf(2.f, y.y, -pv.y));
+        out.z = fmaf(ci, v.z, fmaf(2.f, y.z, -pv.z));
+        out.w = fmaf(ci, v.w, fmaf(2.f, y.w, -pv.w));
+        *reinterpret_cast<float4*>(args.lam_out + row * MP + p0) = out;
+    }
+}
+
+template <int MP, typename VT>
+static cudaError_t launch_adj_mp(int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+    switch (mode) {
+        case 0: adjoint_kernel<MP, VT, 0><<<grid, kThreads, 0, s>>>(a); break;
+        case 1: adjoint_kernel<MP, VT, 1><<<grid, kThreads, 0, s>>>(a); break;
+        case 2: adjoint_kernel<MP, VT, 2><<<grid, kThreads, 0, s>>>(a); break;
+        case 3: adjoint_kernel<MP, VT, 3><<<grid, kThreads, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t launch_adj_vt(int panel, int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+    switch (panel) {
+        case 4: return launch_adj_mp<4, VT>(mode, grid, s, a);
+        case 8: return launch_adj_mp<8, VT>(mode, grid, s, a);
+        case 16: return launch_adj_mp<16, VT>(mode, grid, s, a);
+        case 32: return launch_adj_mp<32, VT>(mode, grid, s, a);
+        case 64: return launch_adj_mp<64, VT>(mode, grid, s, a);
+        case 128: return launch_adj_mp<128, VT>(mode, grid, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+// G[pos(r,k)] = gscale * H[pos(k,r)]: for every stored (r, k), the first stored
+// (k, r) of row k.  flags bit 16: the pattern is not symmetric.
+__global__ void adjoint_gather_kernel(int64_t d, const int64_t* __restrict__ rowptr,
+                                      const int32_t* __restrict__ col, const float* __restrict__ H,
+                                      double gscale, float* __restrict__ G, uint32_t* flags) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < d;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t pos = rowptr[r]; pos < rowptr[r + 1]; ++pos) {
+            const int64_t k = col[pos];
+            int64_t hit = -1;
+            for (int64_t q = rowptr[k]; q < rowptr[k + 1]; ++q)
+                if (col[q] == r) { hit = q; break; }
+            if (hit < 0) {
+                atomicOr(flags, 0x10000u);
+                G[pos] = 0.f;
+            } else {
+                G[pos] = (float)(gscale * (double)H[hit]);
+            }
+        }
+    }
+}
+
+cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+    switch (dtype) {
+        case 0: return launch_adj_vt<float>(panel, mode, grid, s, a);
+        case 1: return launch_adj_vt<bf16_t>(panel, mode, grid, s, a);
+        case 2: return launch_adj_vt<double>(panel, mode, grid, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_adjoint_gather(int64_t d, const int64_t* rowptr, const int32_t* col, const float* H,
+                                  double gscale, float* G, uint32_t* flags, int grid, cudaStream_t s) {
+    adjoint_gather_kernel<<<grid, kThreads, 0, s>>>(d, rowptr, col, H, gscale, G, flags);
+    return cudaGetLastError();
+}
+
+}  // namespace cld

@@ -139,12 +139,9 @@ __device__ double block_max(double v, double* sh) {
     return r;
 }
 
-__global__ void finalize_kernel(int n, int M, int64_t d, int general, const Params* prm,
-                                double* __restrict__ T, double* __restrict__ coeffs,
-                                double* __restrict__ scratch, double* __restrict__ gamma_p,
-                                Result* res) {
-    __shared__ double sh[kThreads];
-    const double a = prm->a, b = prm->b;
+// c_0..c_n into coeffs, by one CTA (scratch: 5 (n+1) doubles).
+__device__ void chebyshev_coefficients(int n, double a, double b, double* __restrict__ coeffs,
+                                       double* __restrict__ scratch) {
     const int N = n + 1;
     double* tab = scratch;          // 4N
     double* f = scratch + 4 * N;    // N
@@ -164,6 +161,24 @@ __global__ void finalize_kernel(int n, int M, int64_t d, int general, const Para
         }
         coeffs[j] = (j == 0 ? 1.0 : 2.0) * s / N;
     }
+}
+
+__global__ void coeffs_kernel(int n, const Params* prm, double* __restrict__ coeffs,
+                              double* __restrict__ scratch) {
+    chebyshev_coefficients(n, prm->a, prm->b, coeffs, scratch);
+}
+
+cudaError_t launch_coeffs(int n, const Params* prm, double* coeffs, double* coef_scratch, cudaStream_t s) {
+    coeffs_kernel<<<1, kThreads, 0, s>>>(n, prm, coeffs, coef_scratch);
+    return cudaGetLastError();
+}
+
+__global__ void finalize_kernel(int n, int M, int64_t d, int general, const Params* prm,
+                                double* __restrict__ T, double* __restrict__ coeffs,
+                                double* __restrict__ scratch, double* __restrict__ gamma_p,
+                                Result* res) {
+    __shared__ double sh[kThreads];
+    chebyshev_coefficients(n, prm->a, prm->b, coeffs, scratch);
     for (int p = threadIdx.x; p < M; p += blockDim.x) T[p] = (double)d;
     __syncthreads();
 

@@ -90,6 +90,7 @@ struct cld_ctx {
 struct Layout {
     size_t params, result, flags, rowptrT, colT, valT, tscratch, run;  // fixed part
     size_t coeffs, coef_scratch, T, gamma_p, tpart, gpart, vbits, W[3], Y, lanczos, total;
+    size_t Wall, lam[3], H;  // gradient: w_1..w_n, the adjoint ring, per-entry sums
     int panel, nw, grid, ggrid;
 };
 
@@ -148,7 +149,11 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
     // large enough, else gets its own region.
     const size_t lz = align_up((size_t)5 * h->d * 8) + align_up((size_t)(8000 + L.ggrid + 64) * 8);
     if (lz > 3 * wb) { L.lanczos = o; o += lz; } else { L.lanczos = L.W[0]; }
-    (void)with_grad;
+    if (with_grad) {
+        L.Wall = o; o += (size_t)(nn > 0 ? nn : 1) * wb;
+        for (int i = 0; i < 3; ++i) { L.lam[i] = o; o += wb; }
+        L.H = o; o += align_up((size_t)h->nnz * 4);
+    }
     L.total = o;
     return L;
 }
@@ -295,79 +300,125 @@ cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a_out, dou
     return CLD_OK;
 }
 
-static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed) {
+// Buffer of w_m (m >= 1): the 3-buffer ring, or (store_all) buffer m-1 of Wall.
+static float* wbuf(cld_ctx* h, const Layout& L, int m, bool store_all) {
+    if (store_all) return reinterpret_cast<float*>(h->ws + L.Wall + (size_t)(m - 1) * (L.W[1] - L.W[0]));
+    return at<float>(h, L.W[m % 3]);
+}
+
+// Enqueues the probe signs and the n recurrence steps of panel pk, then the
+// moment reduction of that panel.  Counts launches.
+static cld_status enqueue_panel_forward(cld_ctx* h, const Layout& L, int n, int M, int pk, bool store_all,
+                                        int* launches, int* step_launches) {
     Params* prm = at<Params>(h, L.params);
-    double* T = at<double>(h, L.T);
     double* tpart = at<double>(h, L.tpart);
     uint32_t* vbits = at<uint32_t>(h, L.vbits);
-    float* W[3] = {at<float>(h, L.W[0]), at<float>(h, L.W[1]), at<float>(h, L.W[2])};
     float* Y = h->kind == CLD_GENERAL ? at<float>(h, L.Y) : nullptr;
     const bool general = h->kind == CLD_GENERAL;
     const int64_t* rpT = general ? at<int64_t>(h, L.rowptrT) : h->rowptr;
     const int32_t* colT = general ? at<int32_t>(h, L.colT) : h->col;
     const void* valT = general ? at<void>(h, L.valT) : h->val;
-    int launches = 0, step_launches = 0;
-    int npanels = (M + kMaxPanel - 1) / kMaxPanel;
-    if (h->profiling) {
-        while ((int)h->ev.size() < 2 * npanels) {
-            cudaEvent_t e;
-            CUDA_TRY(cudaEventCreate(&e));
-            h->ev.push_back(e);
+    const int pbase = pk * kMaxPanel;
+    const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
+    CUDA_TRY(launch_probe_bits(h->d, L.nw, (uint32_t)pk, prm, vbits, L.ggrid, h->stream));
+    ++*launches;
+    StepArgs a{};
+    a.d = h->d;
+    a.vbits = vbits;
+    a.prm = prm;
+    a.mreal = mreal;
+    a.impl = h->impl;
+    for (int j = 0; j < n; ++j) {
+        // w_{j+1} <- step j; w_j and w_{j-1} from the previous steps (w_0 = v).
+        if (h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
+        const float* wj = j >= 1 ? wbuf(h, L, j, store_all) : nullptr;
+        const float* wjm = j >= 2 ? wbuf(h, L, j - 1, store_all) : nullptr;
+        float* wout = wbuf(h, L, j + 1, store_all);
+        a.tpart = tpart + (size_t)j * L.grid * L.panel;
+        StepKind kind;
+        if (general) {
+            // y = C w_j, then w_{j+1} from C^T y
+            StepArgs p = a;
+            p.rowptr = h->rowptr; p.col = h->col; p.val = h->val;
+            p.x = wj; p.out = Y;
+            CUDA_TRY(launch_step(L.panel, (int)h->dtype, j == 0 ? kProdBits : kProdFloat, L.grid,
+                                 h->stream, p));
+            ++*launches;
+            a.rowptr = rpT; a.col = colT; a.val = valT;
+            a.x = Y; a.own = wj; a.wprev = wjm; a.out = wout;
+            kind = j == 0 ? kStepFirstFromFloat : j == 1 ? kStepSecond : kStepGeneral;
+        } else {
+            a.rowptr = h->rowptr; a.col = h->col; a.val = h->val;
+            a.x = wj; a.own = wj; a.wprev = wjm; a.out = wout;
+            kind = j == 0 ? kStepFirst : j == 1 ? kStepSecond : kStepGeneral;
         }
+        CUDA_TRY(launch_step(L.panel, (int)h->dtype, kind, L.grid, h->stream, a));
+        ++*launches;
+        if (j >= 2) ++*step_launches;
     }
+    if (h->profiling && n >= 3) CUDA_TRY(cudaEventRecord(h->ev[2 * pk + 1], h->stream));
+    if (n > 0) {
+        CUDA_TRY(launch_reduce_moments(tpart, n, L.grid, L.panel, mreal, M, pbase, at<double>(h, L.T),
+                                       h->stream));
+        ++*launches;
+    }
+    return CLD_OK;
+}
+
+static cld_status ensure_events(cld_ctx* h, int M) {
+    const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+    while (h->profiling && (int)h->ev.size() < 2 * npanels) {
+        cudaEvent_t e;
+        CUDA_TRY(cudaEventCreate(&e));
+        h->ev.push_back(e);
+    }
+    return CLD_OK;
+}
+
+static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed) {
+    Params* prm = at<Params>(h, L.params);
+    int launches = 0, step_launches = 0;
+    const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+    cld_status st = ensure_events(h, M);
+    if (st != CLD_OK) return st;
     CUDA_TRY(launch_set_seed(prm, seed, h->stream));
     ++launches;
     for (int pk = 0; pk < npanels; ++pk) {
-        const int pbase = pk * kMaxPanel;
-        const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
-        CUDA_TRY(launch_probe_bits(h->d, L.nw, (uint32_t)pk, prm, vbits, L.ggrid, h->stream));
-        ++launches;
-        StepArgs a{};
-        a.d = h->d;
-        a.vbits = vbits;
-        a.prm = prm;
-        a.mreal = mreal;
-        a.impl = h->impl;
-        for (int j = 0; j < n; ++j) {
-            // w_{j+1} lives in W[(j+1) % 3]; w_j in W[j % 3] (j >= 1); w_0 = v.
-            if (h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
-            const float* wj = j >= 1 ? W[j % 3] : nullptr;
-            const float* wjm = j >= 2 ? W[(j - 1) % 3] : nullptr;
-            float* wout = W[(j + 1) % 3];
-            a.tpart = tpart + (size_t)j * L.grid * L.panel;
-            StepKind kind;
-            if (general) {
-                // y = C w_j, then w_{j+1} from C^T y
-                StepArgs p = a;
-                p.rowptr = h->rowptr; p.col = h->col; p.val = h->val;
-                p.x = wj; p.out = Y;
-                CUDA_TRY(launch_step(L.panel, (int)h->dtype, j == 0 ? kProdBits : kProdFloat, L.grid,
-                                     h->stream, p));
-                ++launches;
-                a.rowptr = rpT; a.col = colT; a.val = valT;
-                a.x = Y; a.own = wj; a.wprev = wjm; a.out = wout;
-                kind = j == 0 ? kStepFirstFromFloat : j == 1 ? kStepSecond : kStepGeneral;
-            } else {
-                a.rowptr = h->rowptr; a.col = h->col; a.val = h->val;
-                a.x = wj; a.own = wj; a.wprev = wjm; a.out = wout;
-                kind = j == 0 ? kStepFirst : j == 1 ? kStepSecond : kStepGeneral;
-            }
-            CUDA_TRY(launch_step(L.panel, (int)h->dtype, kind, L.grid, h->stream, a));
-            ++launches;
-            if (j >= 2) ++step_launches;
-        }
-        if (h->profiling && n >= 3) CUDA_TRY(cudaEventRecord(h->ev[2 * pk + 1], h->stream));
-        if (n > 0) {
-            CUDA_TRY(launch_reduce_moments(tpart, n, L.grid, L.panel, mreal, M, pbase, T, h->stream));
-            ++launches;
-        }
+        st = enqueue_panel_forward(h, L, n, M, pk, false, &launches, &step_launches);
+        if (st != CLD_OK) return st;
     }
-    CUDA_TRY(launch_finalize(n, M, h->d, general ? 1 : 0, prm, T, at<double>(h, L.coeffs),
-                             at<double>(h, L.coef_scratch), at<double>(h, L.gamma_p),
+    CUDA_TRY(launch_finalize(n, M, h->d, h->kind == CLD_GENERAL ? 1 : 0, prm, at<double>(h, L.T),
+                             at<double>(h, L.coeffs), at<double>(h, L.coef_scratch), at<double>(h, L.gamma_p),
                              at<Result>(h, L.result), h->stream));
     ++launches;
     h->last_total_launches = launches;
     h->last_step_launches = step_launches;
+    return CLD_OK;
+}
+
+static cld_status read_result(cld_ctx* h, const Layout& L, int n, int M, double* logdet_out, double* stderr_out,
+                              double* moments_out, Result* r) {
+    CUDA_TRY(cudaMemcpyAsync(r, at<Result>(h, L.result), sizeof(Result), cudaMemcpyDeviceToHost, h->stream));
+    if (moments_out)
+        CUDA_TRY(cudaMemcpyAsync(moments_out, at<double>(h, L.T), sizeof(double) * (size_t)(n + 1) * M,
+                                 cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (h->profiling && n >= 3) {
+        float total = 0.f;
+        const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+        for (int pk = 0; pk < npanels; ++pk) {
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2 * pk], h->ev[2 * pk + 1]));
+            total += ms;
+        }
+        h->last_step_ms = total;
+    } else {
+        h->last_step_ms = 0.f;
+    }
+    *logdet_out = r->logdet;
+    if (stderr_out) *stderr_out = r->stderr_;
+    h->last_n = n;
+    h->last_M = M;
     return CLD_OK;
 }
 
@@ -393,28 +444,8 @@ cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logde
     cld_status st = enqueue_estimate(h, L, n, M, seed);
     if (st != CLD_OK) return st;
     Result r{};
-    CUDA_TRY(cudaMemcpyAsync(&r, at<Result>(h, L.result), sizeof(Result), cudaMemcpyDeviceToHost,
-                             h->stream));
-    if (moments_out)
-        CUDA_TRY(cudaMemcpyAsync(moments_out, at<double>(h, L.T), sizeof(double) * (size_t)(n + 1) * M,
-                                 cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (h->profiling && n >= 3) {
-        float total = 0.f;
-        const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
-        for (int pk = 0; pk < npanels; ++pk) {
-            float ms = 0.f;
-            CUDA_TRY(cudaEventElapsedTime(&ms, h->ev[2 * pk], h->ev[2 * pk + 1]));
-            total += ms;
-        }
-        h->last_step_ms = total;
-    } else {
-        h->last_step_ms = 0.f;
-    }
-    *logdet_out = r.logdet;
-    if (stderr_out) *stderr_out = r.stderr_;
-    h->last_n = n;
-    h->last_M = M;
+    st = read_result(h, L, n, M, logdet_out, stderr_out, moments_out, &r);
+    if (st != CLD_OK) return st;
     if (r.spectrum_bad)
         return fail(CLD_ERR_SPECTRUM,
                     "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]", r.max_ratio,
@@ -437,9 +468,87 @@ cld_status cld_last_details(cld_handle h, double* coeffs_out, double* gamma_p_ou
 }
 
 cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out, float* dvalues_dev) {
-    (void)n; (void)M; (void)seed; (void)logdet_out; (void)dvalues_dev;
     if (check_handle(h)) return CLD_ERR_INVALID;
-    return fail(CLD_ERR_UNSUPPORTED, "cld_grad is not built yet");
+    if (h->kind != CLD_SPD) return fail(CLD_ERR_UNSUPPORTED, "cld_grad supports CLD_SPD matrices only");
+    if (n < 0 || M < 1 || n > 100000) return fail(CLD_ERR_INVALID, "need 0 <= n <= 100000 and M >= 1");
+    if (!logdet_out) return fail(CLD_ERR_INVALID, "logdet_out is NULL");
+    if (!dvalues_dev && h->nnz > 0) return fail(CLD_ERR_INVALID, "dvalues_dev is NULL");
+    if (!h->have_interval) return fail(CLD_ERR_INTERVAL, "no spectral interval set");
+    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
+    const Layout L = make_layout(h, n, M, 1);
+    if (h->ws_bytes < L.total)
+        return fail(CLD_ERR_NOMEM, "gradient workspace has %zu bytes, %zu needed", h->ws_bytes, L.total);
+    h->last_n = -1;
+    if (h->d == 0) {
+        *logdet_out = 0.0;
+        return CLD_OK;
+    }
+    Params* prm = at<Params>(h, L.params);
+    uint32_t* flags = at<uint32_t>(h, L.flags);
+    float* H = at<float>(h, L.H);
+    int launches = 0, step_launches = 0;
+    cld_status st = ensure_events(h, M);
+    if (st != CLD_OK) return st;
+    CUDA_TRY(cudaMemsetAsync(flags, 0, 4, h->stream));
+    CUDA_TRY(cudaMemsetAsync(H, 0, (size_t)h->nnz * 4, h->stream));
+    CUDA_TRY(launch_set_seed(prm, seed, h->stream));
+    CUDA_TRY(launch_coeffs(n, prm, at<double>(h, L.coeffs), at<double>(h, L.coef_scratch), h->stream));
+    launches += 2;
+    const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+    float* lam[3] = {at<float>(h, L.lam[0]), at<float>(h, L.lam[1]), at<float>(h, L.lam[2])};
+    for (int pk = 0; pk < npanels; ++pk) {
+        st = enqueue_panel_forward(h, L, n, M, pk, true, &launches, &step_launches);
+        if (st != CLD_OK) return st;
+        if (n == 0) continue;
+        const int mreal = (M - pk * kMaxPanel) < L.panel ? (M - pk * kMaxPanel) : L.panel;
+        AdjArgs a{};
+        a.d = h->d;
+        a.rowptr = h->rowptr;
+        a.col = h->col;
+        a.val = h->val;
+        a.vbits = at<uint32_t>(h, L.vbits);
+        a.H = H;
+        a.coeffs = at<double>(h, L.coeffs);
+        a.prm = prm;
+        a.mreal = mreal;
+        // lambda_i lives in lam[i % 3]
+        for (int i = n; i >= 1; --i) {
+            a.ci = i;
+            a.lam_out = lam[i % 3];
+            a.lam_in = lam[(i + 1) % 3];
+            a.lam_prev = lam[(i + 2) % 3];
+            a.w = i <= n - 1 ? wbuf(h, L, i, true) : nullptr;
+            const int mode = i == n ? 0 : i == n - 1 ? 1 : 2;
+            CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, mode, L.grid, h->stream, a));
+            ++launches;
+        }
+        a.lam_in = lam[1 % 3];  // lambda_1
+        a.lam_out = nullptr;
+        a.w = nullptr;
+        CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, 3, L.grid, h->stream, a));
+        ++launches;
+    }
+    CUDA_TRY(launch_finalize(n, M, h->d, 0, prm, at<double>(h, L.T), at<double>(h, L.coeffs),
+                             at<double>(h, L.coef_scratch), at<double>(h, L.gamma_p), at<Result>(h, L.result),
+                             h->stream));
+    ++launches;
+    if (h->nnz > 0) {
+        CUDA_TRY(launch_adjoint_gather(h->d, h->rowptr, h->col, H, 2.0 / (h->b - h->a) / M, dvalues_dev, flags,
+                                       L.ggrid, h->stream));
+        ++launches;
+    }
+    h->last_total_launches = launches;
+    h->last_step_launches = step_launches;
+    uint32_t f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+    Result r{};
+    st = read_result(h, L, n, M, logdet_out, nullptr, nullptr, &r);
+    if (st != CLD_OK) return st;
+    if (f & 0x10000u) return fail(CLD_ERR_INVALID, "cld_grad needs a structurally symmetric sparsity pattern");
+    if (r.spectrum_bad)
+        return fail(CLD_ERR_SPECTRUM, "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]",
+                    r.max_ratio, h->a, h->b);
+    return CLD_OK;
 }
 
 cld_status cld_host_workspace_size(int64_t d, int64_t nnz, cld_dtype val_dtype, int n, int M,

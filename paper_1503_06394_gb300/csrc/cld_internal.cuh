@@ -156,5 +156,28 @@ cudaError_t launch_gershgorin(int64_t d, const int64_t* rowptr, const int32_t* c
                               const void* val, int dtype, double* partial, int grid,
                               Params* prm, uint32_t* flags, cudaStream_t s);
 cudaError_t launch_set_params(Params* prm, double a, double b, cudaStream_t s);
+cudaError_t launch_coeffs(int n, const Params* prm, double* coeffs, double* coef_scratch, cudaStream_t s);
+
+// ------------------------------------------------------------------ adjoint (adjoint.cu)
+// Arguments of one adjoint pass (see adjoint.cu).
+struct AdjArgs {
+    int64_t d;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const void* val;
+    const float* lam_in;     // lambda_{i+1} (gathered)
+    const float* lam_prev;   // lambda_{i+2}
+    float* lam_out;          // lambda_i
+    const float* w;          // w_i (own rows), MODE 1..2
+    const uint32_t* vbits;
+    float* H;                // nnz accumulators, by stored position
+    const double* coeffs;    // c_0..c_n
+    int ci;                  // i
+    const Params* prm;
+    int mreal;
+};
+cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a);
+cudaError_t launch_adjoint_gather(int64_t d, const int64_t* rowptr, const int32_t* col, const float* H,
+                                  double gscale, float* G, uint32_t* flags, int grid, cudaStream_t s);
 
 }  // namespace cld

@@ -145,7 +145,6 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
     constexpr int GPW = 32 / LPR;        // rows per warp
     constexpr int NW = MP <= 32 ? 1 : MP / 32;
     constexpr int WPB = kThreads / 32;
-    constexpr int U = 4;                 // stored entries in flight per group
 
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;

@@ -192,19 +192,20 @@ def nonsymmetric_dominant(d: int, picks: int, seed: int) -> Csr:
                           "nonsymmetric_dominant(d=%d,picks=%d,seed=%d)" % (d, picks, seed))
 
 
-def wendland(npts: int, ell: float, sigma2: float, seed: int) -> tuple[Csr, np.ndarray]:
-    """(K + sigma2 I as Csr, points npts x 2)."""
+def wendland_pattern(npts: int, ell: float, seed: int):
+    """(Csr of distances with the diagonal stored as 0, points npts x 2): all
+    pairs of uniform points in the unit square closer than ell, plus the
+    diagonal, sorted rows.  Values are the pair distances."""
     rng = np.random.default_rng(seed)
     pts = rng.random((npts, 2))
-    # cell list with cell size ell: neighbours lie in the 3x3 block of cells
+    # cell list with cells of side >= ell: neighbours lie in the 3 x 3 block
     ncell = max(1, int(np.floor(1.0 / ell)))
     cx = np.minimum((pts[:, 0] * ncell).astype(np.int64), ncell - 1)
     cy = np.minimum((pts[:, 1] * ncell).astype(np.int64), ncell - 1)
     cell = cx * ncell + cy
     order = np.argsort(cell, kind="stable")
-    cell_sorted = cell[order]
-    starts = np.searchsorted(cell_sorted, np.arange(ncell * ncell + 1))
-    rows_l, cols_l, vals_l = [], [], []
+    starts = np.searchsorted(cell[order], np.arange(ncell * ncell + 1))
+    rows_l, cols_l, dist_l = [], [], []
     for ox in (-1, 0, 1):
         for oy in (-1, 0, 1):
             nx, ny = cx + ox, cy + oy
@@ -214,21 +215,35 @@ def wendland(npts: int, ell: float, sigma2: float, seed: int) -> tuple[Csr, np.n
             lo, hi = starts[nb], starts[nb + 1]
             cnt = hi - lo
             rep = np.repeat(src, cnt)
-            offs = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+            offs = np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt)
             tgt = order[np.repeat(lo, cnt) + offs]
             dist = np.sqrt(((pts[rep] - pts[tgt]) ** 2).sum(axis=1))
-            rr = dist / ell
-            keep = (rr < 1.0) & (rep != tgt)
-            q = 1.0 - rr[keep]
+            keep = (dist < ell) & (rep != tgt)
             rows_l.append(rep[keep])
             cols_l.append(tgt[keep])
-            vals_l.append(q ** 4 * (4.0 * rr[keep] + 1.0))
+            dist_l.append(dist[keep])
     rows_l.append(np.arange(npts))
     cols_l.append(np.arange(npts))
-    vals_l.append(np.full(npts, 1.0 + sigma2))
-    K = _coo_to_csr(npts, np.concatenate(rows_l), np.concatenate(cols_l), np.concatenate(vals_l),
-                    "wendland(n=%d,ell=%g,sigma2=%g,seed=%d)" % (npts, ell, sigma2, seed))
-    return K, pts
+    dist_l.append(np.zeros(npts))
+    # a stored 0 distance on the diagonal must survive the duplicate summation
+    P = _coo_to_csr(npts, np.concatenate(rows_l), np.concatenate(cols_l), np.concatenate(dist_l) + 1.0,
+                    "wendland_pattern(n=%d,ell=%g,seed=%d)" % (npts, ell, seed))
+    P.val -= 1.0
+    return P, pts
+
+
+def wendland_values(dist: np.ndarray, is_diag: np.ndarray, ell: float, sigma2: float) -> np.ndarray:
+    """K_rk = (1 - r)^4 (4 r + 1), r = dist / ell, off the diagonal; 1 + sigma2 on it."""
+    r = dist / ell
+    return np.where(is_diag, 1.0 + sigma2, (1.0 - r) ** 4 * (4.0 * r + 1.0))
+
+
+def wendland(npts: int, ell: float, sigma2: float, seed: int) -> tuple[Csr, np.ndarray]:
+    """(K + sigma2 I as Csr, points npts x 2)."""
+    P, pts = wendland_pattern(npts, ell, seed)
+    rows = np.repeat(np.arange(npts), np.diff(P.rowptr))
+    vals = wendland_values(P.val, rows == P.col, ell, sigma2)
+    return Csr(P.rowptr, P.col, vals, "wendland(n=%d,ell=%g,sigma2=%g,seed=%d)" % (npts, ell, sigma2, seed)), pts
 
 
 def apex_graph(nv: int, extra_edges: int, seed: int) -> Csr:
@@ -258,10 +273,13 @@ CONFIGS = {
     0: dict(kind="sparse_random_spd", d=2048, picks=3, seed=1000, n=30, M=30, probe_seed=0),
     1: dict(kind="grid_gmrf", N=1000, kappa2=0.1, n=50, M=64, probe_seed=0),
     2: dict(kind="sparse_random_spd", d=10_000_000, picks=5, seed=1002, n=100, M=32, probe_seed=0),
+    3: dict(kind="wendland", npts=1_000_000, ell=0.002, sigma2=0.1, seed=1003, n=60, M=32, probe_seed=0),
 }
 
 
 def make(cfg: dict) -> Csr:
+    if cfg["kind"] == "wendland":
+        return wendland(cfg["npts"], cfg["ell"], cfg["sigma2"], cfg["seed"])[0]
     if cfg["kind"] == "sparse_random_spd":
         return sparse_random_spd(cfg["d"], cfg["picks"], cfg["seed"])
     if cfg["kind"] == "grid_gmrf":
