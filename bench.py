@@ -277,6 +277,10 @@ def run_ours(args, rank, world):
         del m16
         torch.cuda.empty_cache()
 
+    adjoint = None
+    if not args.no_adjoint and args.d is None:
+        adjoint = adjoint_leg(args, torch, world)
+
     # end to end through the host-buffer entry point (pinned host arrays)
     rp = torch.from_numpy(B.rowptr).pin_memory()
     cl = torch.from_numpy(B.col).pin_memory()
@@ -322,6 +326,8 @@ def run_ours(args, rank, world):
             "clocks": clk.summary(), "generation_s": gen_s}
     if bf16 is not None:
         line["bf16"] = bf16
+    if adjoint is not None:
+        line["adjoint"] = adjoint
     if not args.no_cpu_baseline:
         # the oracle on the original FP64 values, probe 0: the CPU baseline and
         # the reference for the relative errors of the FP32 and BF16 results
@@ -339,6 +345,49 @@ def run_ours(args, rank, world):
             if bf16 is not None:
                 bf16["rel_err_probe0_vs_fp64_oracle"] = abs(bf16["gamma_p0"] - gp0) / abs(gp0)
     print(json.dumps(line), flush=True)
+
+
+def adjoint_leg(args, torch, world):
+    """Config 3: Wendland kernel matrix (1e6 points, ell = 0.002, sigma2 = 0.1),
+    n = 60, M = 32.  Times cld_estimate (forward) and cld_grad (forward storing
+    every w_j + reverse pass + gradient map) on the same matrix and probes."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    cfg = workloads.CONFIGS[3]
+    K = workloads.make(cfg)
+    v32, _ = K.stored("f32")
+    n, M = cfg["n"], cfg["M"]
+    a = cfg["sigma2"]
+    b = float(np.max(np.add.reduceat(np.abs(v32.astype(np.float64)), K.rowptr[:-1])))
+    m = CsrLogdet(K.rowptr, K.col, v32)
+    m.set_interval(a, b)
+    m.autotune(n, M)
+    m.reserve(n, M, 1)
+    m.estimate(n, M, 0)
+    m.grad(n, M, 0)
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    steps = max(1, args.steps)
+    torch.cuda.synchronize()
+    e[0].record(stream)
+    for _ in range(steps):
+        r = m.estimate(n, M, 0)
+    e[1].record(stream)
+    for _ in range(steps):
+        g, G = m.grad(n, M, 0)
+    e[2].record(stream)
+    torch.cuda.synchronize()
+    fwd = e[0].elapsed_time(e[1]) / steps
+    grd = e[1].elapsed_time(e[2]) / steps
+    m.close()
+    del m, G
+    torch.cuda.empty_cache()
+    return {"workload": "wendland npts=%d ell=%g sigma2=%g (nnz=%d, %.1f per row), n=%d, M=%d" % (
+                cfg["npts"], cfg["ell"], cfg["sigma2"], K.nnz, K.nnz / K.d, n, M),
+            "interval": [a, b], "forward_ms": fwd, "grad_ms": grd,
+            "adjoint_forward_ratio": grd / fwd, "reverse_over_forward": (grd - fwd) / fwd,
+            "storage": "all w_j kept in HBM (%.1f GB)" % (n * K.d * 32 * 4 / 1e9),
+            "logdet": r["logdet"], "grad_logdet": g}
 
 
 def profiled_traffic(args, B):
@@ -373,6 +422,7 @@ def main():
     ap.add_argument("--d", type=int, default=None, help="override the dimension (small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage measurement")
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward (config 3) measurement")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

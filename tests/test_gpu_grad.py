@@ -180,3 +180,22 @@ def test_autograd_hyperparameters_vs_cholesky_trace(torch):
         mean, se = np.mean(est), np.std(est, ddof=1) / np.sqrt(len(est))
         print("grad mean %.4f +- %.4f exact %.4f" % (mean, se, exact))
         assert abs(mean - exact) <= 5 * se + 1e-3 * abs(exact)
+
+
+def test_grad_config3_full_sampled(torch):
+    """Config 3 at full size (1e6 Wendland points, n = 60): the gradient for 4
+    probes against the oracle adjoint on the same probes, on a sample of 20,000
+    stored entries (and the max over all entries within the same bound)."""
+    cfg = workloads.CONFIGS[3]
+    K = workloads.make(cfg)
+    v32, v64 = K.stored("f32")
+    a = cfg["sigma2"]
+    b = float(np.max(np.add.reduceat(np.abs(v64), K.rowptr[:-1])))
+    n, M, seed = cfg["n"], 4, 7
+    g, G, est = gpu_grad(K, v32, a, b, n, M, seed)
+    V = oracle.rademacher(seed, K.d, np.arange(M))
+    Gref = oracle.grad(K.rowptr, K.col, v64, a, b, n, V)
+    scale = np.max(np.abs(Gref))
+    idx = np.random.default_rng(0).choice(K.nnz, 20000, replace=False)
+    assert np.max(np.abs(G[idx] - Gref[idx])) <= 2e-5 * scale
+    assert np.max(np.abs(G - Gref)) <= 2e-5 * scale
