@@ -22,6 +22,53 @@ namespace cld {
 
 
 
+// The per-entry probe sums of a 4-entry chunk are reduced across the LPR lanes
+// of a row group with a reduce-scatter: after it, entry q's full sum sits in
+// one lane (two entries per lane when LPR = 2, all four when LPR = 1).
+// adj_owned_entries gives the entries a lane owns (-1: none).
+template <int LPR>
+__device__ __forceinline__ void adj_owned_entries(int lig, int& qa, int& qb) {
+    if (LPR == 1) { qa = -1; qb = -1; }                      // handled as 4 entries below
+    else if (LPR == 2) { qa = 2 * lig; qb = 2 * lig + 1; }
+    else if (LPR == 4) { qa = lig; qb = -1; }
+    else { qa = (lig & 1) == 0 && lig < 8 ? (lig >> 1) : -1; qb = -1; }
+}
+
+template <int LPR>
+__device__ __forceinline__ void adj_reduce_scatter4(float (&dt)[4], int lig, unsigned gmask, float& sa, float& sb) {
+    sa = 0.f;
+    sb = 0.f;
+    if (LPR == 1) return;
+    if (LPR == 2) {
+        // lane 0 keeps entries 0,1; lane 1 keeps 2,3
+        const bool hi = lig & 1;
+        const float s0 = hi ? dt[0] : dt[2], s1 = hi ? dt[1] : dt[3];
+        const float r0 = __shfl_xor_sync(gmask, s0, 1, LPR), r1 = __shfl_xor_sync(gmask, s1, 1, LPR);
+        sa = (hi ? dt[2] : dt[0]) + r0;
+        sb = (hi ? dt[3] : dt[1]) + r1;
+        return;
+    }
+    // fold the upper lanes until 8 (or 4) remain
+#pragma unroll
+    for (int off = LPR / 2; off >= 8; off >>= 1) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(gmask, dt[u], off, LPR);
+    }
+    constexpr int W = LPR >= 8 ? 8 : 4;
+    // stage A over xor W/2: keep entries {0,1} or {2,3}
+    const bool ha = (lig & (W / 2)) != 0;
+    const float s0 = ha ? dt[0] : dt[2], s1 = ha ? dt[1] : dt[3];
+    float k0 = (ha ? dt[2] : dt[0]) + __shfl_xor_sync(gmask, s0, W / 2, LPR);
+    float k1 = (ha ? dt[3] : dt[1]) + __shfl_xor_sync(gmask, s1, W / 2, LPR);
+    // stage B over xor W/4: keep one entry
+    const bool hb = (lig & (W / 4)) != 0;
+    const float snd = hb ? k0 : k1;
+    float kk = (hb ? k1 : k0) + __shfl_xor_sync(gmask, snd, W / 4, LPR);
+    // stage C (W = 8 only): finish over xor 1
+    if (W == 8) kk += __shfl_xor_sync(gmask, kk, 1, LPR);
+    sa = kk;
+}
+
 // MODE 0: lambda_{i+1} = 0 (i = n): lambda_i = c_i v; no gather, no H term.
 // MODE 1: lambda_{i+2} = 0 (i = n - 1).
 // MODE 2: general.
@@ -60,6 +107,16 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs args) {
         const int64_t k0 = __ldg(args.rowptr + row), k1 = __ldg(args.rowptr + row + 1);
         float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int64_t k = k0; k < k1; k += U) {
+            // this lane's share of the H updates of the chunk, loaded up front
+            int qa, qb;  // entries owned (qb < 0: one entry)
+            adj_owned_entries<LPR>(lig, qa, qb);
+            float ha = 0.f, hb = 0.f, h1[U];
+            if (LPR == 1) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) h1[u] = k + u < k1 ? args.H[k + u] : 0.f;
+            }
+            if (qa >= 0 && k + qa < k1) ha = args.H[k + qa];
+            if (qb >= 0 && k + qb < k1) hb = args.H[k + qb];
             int c[U];
             float a[U];
 #pragma unroll
@@ -73,20 +130,27 @@ __global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs args) {
             for (int u = 0; u < U; ++u)
                 xv[u] = c[u] >= 0 ? __ldg(reinterpret_cast<const float4*>(args.lam_in + (int64_t)c[u] * MP + p0))
                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+            float dt[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 acc.x = fmaf(a[u], xv[u].x, acc.x);
                 acc.y = fmaf(a[u], xv[u].y, acc.y);
                 acc.z = fmaf(a[u], xv[u].z, acc.z);
                 acc.w = fmaf(a[u], xv[u].w, acc.w);
-                float dt = xv[u].x * wk.x;
-                dt = fmaf(xv[u].y, wk.y, dt);
-                dt = fmaf(xv[u].z, wk.z, dt);
-                dt = fmaf(xv[u].w, wk.w, dt);
-#pragma unroll
-                for (int off = LPR / 2; off >= 1; off >>= 1) dt += __shfl_xor_sync(gmask, dt, off, LPR);
-                if (lig == 0 && c[u] >= 0) args.H[k + u] = fmaf(hfac, dt, args.H[k + u]);
+                float t = xv[u].x * wk.x;
+                t = fmaf(xv[u].y, wk.y, t);
+                t = fmaf(xv[u].z, wk.z, t);
+                dt[u] = fmaf(xv[u].w, wk.w, t);
             }
+            if (LPR == 1) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (k + u < k1) args.H[k + u] = fmaf(hfac, dt[u], h1[u]);
+            }
+            float sa, sb;
+            adj_reduce_scatter4<LPR>(dt, lig, gmask, sa, sb);
+            if (qa >= 0 && k + qa < k1) args.H[k + qa] = fmaf(hfac, sa, ha);
+            if (qb >= 0 && k + qb < k1) args.H[k + qb] = fmaf(hfac, sb, hb);
         }
         if (MODE == 3) continue;
         const float4 own = __ldg(reinterpret_cast<const float4*>(args.lam_in + row * MP + p0));

@@ -33,6 +33,7 @@ __device__ __forceinline__ float4 ldcs4(const float* p) {
 }
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
+
 // Row product acc = sum_k X[row, k] * x[k, p0..p0+3] over the stored entries
 // [k0, k1) of one row, for the four probes of this lane.
 //
@@ -139,8 +140,15 @@ __device__ __forceinline__ float4 row_product(int64_t k0, int64_t k1, const int3
 
 // GATHER: 0 float rows of args.x, 1 probe signs.  PREV: 0 none, 1 v, 2 args.wprev.
 // EPI: 0 plain product, 1 recurrence + moments.  IMPL: inner loop (row_product).
+// Resident-CTA targets per variant (256 threads): 6 (40 registers), 3, 4.
+template <int IMPL>
+struct StepOccupancy { static constexpr int value = IMPL == 0 ? 6 : IMPL == 1 ? 3 : 4; };
+
 template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
-__global__ void __launch_bounds__(kThreads) step_kernel(const StepArgs args) {
+__global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_kernel(const StepArgs args);
+
+template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
+__global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_kernel(const StepArgs args) {
     constexpr int LPR = MP / 4;          // lanes per row
     constexpr int GPW = 32 / LPR;        // rows per warp
     constexpr int NW = MP <= 32 ? 1 : MP / 32;
