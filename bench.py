@@ -178,6 +178,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x: float, world: int, device: str = "cpu") -> float:
+    """The slowest rank's time (all ranks take part; identity for one rank)."""
+    if world <= 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_estimates(m, n, M, seed, interval, steps, warmup, torch, world):
     """Warm-up, then `steps` timed estimates (interval + estimate each) with CUDA
     events on the launching stream.  Returns (ms per step, kernel ms per general
@@ -210,11 +221,7 @@ def time_estimates(m, n, M, seed, interval, steps, warmup, torch, world):
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
-    total_ms = float(sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(steps)))
-    if world > 1:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(float(sum(ev[i][0].elapsed_time(ev[i][1]) for i in range(steps))), world, "cuda")
     m.set_profiling(False)
     return total_ms / steps, step_ms / max(1, step_launches), step_launches, total_launches, r
 
