@@ -287,6 +287,9 @@ def run_ours(args, rank, world):
     adjoint = None
     if not args.no_adjoint and args.d is None:
         adjoint = adjoint_leg(args, torch, world)
+    batched = None
+    if not args.no_batch and args.d is None:
+        batched = batch_leg(args, torch)
 
     # end to end through the host-buffer entry point (pinned host arrays)
     rp = torch.from_numpy(B.rowptr).pin_memory()
@@ -335,6 +338,8 @@ def run_ours(args, rank, world):
         line["bf16"] = bf16
     if adjoint is not None:
         line["adjoint"] = adjoint
+    if batched is not None:
+        line["batched"] = batched
     if not args.no_cpu_baseline:
         # the oracle on the original FP64 values, probe 0: the CPU baseline and
         # the reference for the relative errors of the FP32 and BF16 results
@@ -397,6 +402,89 @@ def adjoint_leg(args, torch, world):
             "logdet": r["logdet"], "grad_logdet": g}
 
 
+def batch_bytes(mats, M, s_v, general):
+    """Algorithmic bytes of one degree step over all blocks (no gather reuse)."""
+    tot = 0
+    for m in mats:
+        rows = np.repeat(np.arange(m.d), np.diff(m.rowptr))
+        off = int(np.count_nonzero(m.col != rows))
+        csr = m.nnz * (s_v + 4) + 8 * (m.d + 1)
+        if general:  # y = C w_j (gather w_j, write y), then C^T y (gather y, own, prev, write)
+            tot += 2 * csr + 2 * off * M * 4 + 4 * m.d * M * 4
+        else:
+            tot += csr + off * M * 4 + 3 * m.d * M * 4
+    return tot
+
+
+def batch_leg(args, torch):
+    """Config 4: 512 matrices, d log-uniform in [1e3, 2e5]; the SPD half and the
+    general half (1/2 logdet C^T C) each in one batched estimate replayed as a
+    CUDA graph, against a loop of single-matrix estimates on the same GPU."""
+    from paper_1503_06394_gb300 import CsrBatchLogdet, CsrLogdet
+
+    cfg = workloads.CONFIGS[4]
+    n, M = cfg["n"], cfg["M"]
+    spd, gen = workloads.batch_mixed(cfg["count"], cfg["dmin"], cfg["dmax"], cfg["seed"])
+    out = {"workload": "%d matrices, d log-uniform in [%g, %g] (sum d = %d), half SPD, half general; n=%d, M=%d" % (
+        cfg["count"], cfg["dmin"], cfg["dmax"], sum(m.d for m in spd + gen), n, M)}
+    steps = max(1, args.steps)
+    for dtype in ("f32", "bf16"):
+        tot_ms, tot_bytes = 0.0, 0
+        for kind, mats in (("spd", spd), ("general", gen)):
+            br, S = workloads.block_diag(mats)
+            st, _ = S.stored(dtype)
+            bt = CsrBatchLogdet(br, S.rowptr, S.col, st, dtype=dtype, kind=kind)
+            bt.auto_intervals()
+            v, _ = bt.autotune(n, M)
+            bt.set_graph(True)
+            bt.reserve(n, M)
+            for _ in range(2):
+                bt.estimate(n, M, 0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(steps):
+                r = bt.estimate(n, M, 0)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            bt.close()
+            del bt
+            nbytes = n * batch_bytes(mats, M, 2 if dtype == "bf16" else 4, kind == "general")
+            out["%s_%s_ms" % (kind, dtype)] = ms
+            out["%s_%s_gbs" % (kind, dtype)] = nbytes / (ms / 1e3) / 1e9
+            out["%s_variant" % kind] = v
+            tot_ms += ms
+            tot_bytes += nbytes
+        out["batched_%s_ms" % dtype] = tot_ms
+        out["batched_%s_gbs" % dtype] = tot_bytes / (tot_ms / 1e3) / 1e9
+    # per-matrix loop (FP32): one handle per matrix, estimates one after another
+    handles = []
+    for kind, mats in (("spd", spd), ("general", gen)):
+        for m in mats:
+            v32, _ = m.stored("f32")
+            h = CsrLogdet(m.rowptr, m.col, v32, kind=kind)
+            h.auto_interval(0)
+            h.reserve(n, M)
+            handles.append(h)
+    for h in handles[:4]:
+        h.estimate(n, M, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h in handles:
+        h.estimate(n, M, 0)
+    torch.cuda.synchronize()
+    loop_ms = (time.perf_counter() - t0) * 1e3
+    for h in handles:
+        h.close()
+    del handles
+    torch.cuda.empty_cache()
+    out["loop_f32_ms"] = loop_ms
+    out["speedup_vs_loop"] = loop_ms / out["batched_f32_ms"]
+    out["bf16_vs_f32_time"] = out["batched_bf16_ms"] / out["batched_f32_ms"]
+    return out
+
+
 def profiled_traffic(args, B):
     """DRAM bytes (read + write) per general-step launch from the committed ncu
     summary of this workload, if the step kernel's source is unchanged since."""
@@ -430,6 +518,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward (config 3) measurement")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) measurement")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

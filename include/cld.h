@@ -191,6 +191,48 @@ CLD_API cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t* ro
                                        double a, double b, int n, int M, uint64_t seed,
                                        void* stream, double* logdet_out, double* stderr_out);
 
+/* ------------------------------------------------------------------------ */
+/* Batches: many independent matrices of uneven size estimated together, one */
+/* pass over all of them per degree step (each block is a separate problem   */
+/* of Algorithm 1, or of Algorithm 2 for CLD_GENERAL).                        */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a batch handle.  The nb matrices are given as one block-diagonal
+ * CSR with GLOBAL row and column indices: block b holds rows (and columns)
+ * [blk_rows[b], blk_rows[b+1]); blk_rows is a HOST array of nb+1 offsets,
+ * copied.  rowptr/col/val/val_dtype/kind/stream as in cld_create_csr (all
+ * blocks share the kind).  Block b's probes use the seed seed + b with the
+ * block's local row index, so its estimate equals a single-matrix
+ * cld_estimate of that block with seed + b.  cld_workspace_size and
+ * cld_set_workspace apply (the latter also checks that every column lies in
+ * its row's block).  Errors: CLD_ERR_INVALID. */
+CLD_API cld_status cld_create_batch(cld_handle* out, int nb, const int64_t* blk_rows, int64_t nnz,
+                                    const int64_t* rowptr, const int32_t* col, const void* val,
+                                    cld_dtype val_dtype, cld_kind kind, void* stream);
+
+/* Rows per work tile of the batched step kernel (>= 256; default 1024): a
+ * tile never spans two blocks; CTAs take tiles from a static queue. */
+CLD_API cld_status cld_batch_set_tile_rows(cld_handle h, int rows);
+
+/* Per-block intervals (host arrays of nb doubles), as cld_set_interval. */
+CLD_API cld_status cld_batch_set_intervals(cld_handle h, const double* a, const double* b);
+
+/* Per-block intervals computed on the device as cld_auto_interval (without
+ * Lanczos); written to the host arrays a_out, b_out (nb each, may be NULL). */
+CLD_API cld_status cld_batch_auto_intervals(cld_handle h, double* a_out, double* b_out);
+
+/* Runs all blocks: logdet_out[b] and stderr_out[b] (host arrays of nb; the
+ * latter may be NULL).  Errors as cld_estimate (CLD_ERR_SPECTRUM names the
+ * first failing block; all outputs are still written). */
+CLD_API cld_status cld_batch_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
+                                      double* stderr_out);
+
+/* When on, cld_estimate / cld_batch_estimate replay one CUDA graph of the
+ * whole estimate (captured on first use per (n, M, variant, workspace, tile
+ * size) on a stream of the handle; the seed is set by a launch before it).
+ * Profiling events are not recorded in graph mode. */
+CLD_API cld_status cld_set_graph(cld_handle h, int on);
+
 /* Selects the inner loop of the recurrence-step kernel (a tuning control; all
  * variants compute the same sums in the same order):
  *   0: each lane loads 4 (column, value) pairs itself, 4 row gathers in flight;

@@ -40,6 +40,12 @@ SIGNATURES = [
                                    _vp, _sz, _vp, _P(_f64), _P(_f64)]),
     ("cld_estimate_static", _i32, [_i64, _i64, _vp, _vp, _vp, _i32, _f64, _f64, _i32, _i32, _u64, _vp,
                                    _P(_f64), _P(_f64)]),
+    ("cld_create_batch", _i32, [_P(_vp), _i32, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _vp]),
+    ("cld_batch_set_tile_rows", _i32, [_vp, _i32]),
+    ("cld_batch_set_intervals", _i32, [_vp, _vp, _vp]),
+    ("cld_batch_auto_intervals", _i32, [_vp, _vp, _vp]),
+    ("cld_batch_estimate", _i32, [_vp, _i32, _i32, _u64, _vp, _vp]),
+    ("cld_set_graph", _i32, [_vp, _i32]),
     ("cld_set_kernel_variant", _i32, [_vp, _i32]),
     ("cld_autotune", _i32, [_vp, _i32, _i32, _P(_i32), _P(ctypes.c_float)]),
     ("cld_set_profiling", _i32, [_vp, _i32]),
@@ -174,6 +180,42 @@ def cld_estimate_static(d, nnz, rowptr, col, val, val_dtype, a, b, n, M, seed, s
     _check(load().cld_estimate_static(d, nnz, _ptr(rowptr), _ptr(col), _ptr(val), val_dtype, a, b, n, M, seed,
                                       stream or None, ctypes.byref(g), ctypes.byref(se)))
     return g.value, se.value
+
+
+def cld_create_batch(blk_rows, nnz, rowptr, col, val, val_dtype, kind, stream=0):
+    br = np.ascontiguousarray(blk_rows, dtype=np.int64)
+    h = ctypes.c_void_p()
+    _check(load().cld_create_batch(ctypes.byref(h), br.shape[0] - 1, _ptr(br), nnz, _ptr(rowptr), _ptr(col),
+                                   _ptr(val), val_dtype, kind, stream or None))
+    return h.value
+
+
+def cld_batch_set_tile_rows(h, rows):
+    _check(load().cld_batch_set_tile_rows(h, rows))
+
+
+def cld_batch_set_intervals(h, a, b):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    _check(load().cld_batch_set_intervals(h, _ptr(a), _ptr(b)))
+
+
+def cld_batch_auto_intervals(h, nb):
+    a = np.zeros(nb, dtype=np.float64)
+    b = np.zeros(nb, dtype=np.float64)
+    _check(load().cld_batch_auto_intervals(h, _ptr(a), _ptr(b)))
+    return a, b
+
+
+def cld_batch_estimate(h, nb, n, M, seed):
+    g = np.zeros(nb, dtype=np.float64)
+    se = np.zeros(nb, dtype=np.float64)
+    _check(load().cld_batch_estimate(h, n, M, seed, _ptr(g), _ptr(se)))
+    return g, se
+
+
+def cld_set_graph(h, on):
+    _check(load().cld_set_graph(h, 1 if on else 0))
 
 
 def cld_set_kernel_variant(h, variant):

@@ -100,6 +100,9 @@ class CsrLogdet:
     def set_kernel_variant(self, variant: int):
         B.cld_set_kernel_variant(self.h, variant)
 
+    def set_graph(self, on: bool = True):
+        B.cld_set_graph(self.h, on)
+
     def autotune(self, n: int, M: int, reps: int = 3):
         """Picks the fastest recurrence-step variant for this matrix (n, M
         size the workspace)."""
@@ -125,6 +128,48 @@ class CsrLogdet:
             self.close()
         except Exception:
             pass
+
+
+class CsrBatchLogdet(CsrLogdet):
+    """Many matrices in one block-diagonal CSR (global indices); block b holds
+    rows [blk_rows[b], blk_rows[b+1]).  estimate() returns per-block arrays."""
+
+    def __init__(self, blk_rows, rowptr, col, val, dtype: str = "f32", kind: str = "spd", device="cuda",
+                 stream=None):
+        torch = _torch()
+        self.torch = torch
+        self.device = torch.device(device)
+        self.blk_rows = np.ascontiguousarray(blk_rows, dtype=np.int64)
+        self.nb = int(self.blk_rows.shape[0] - 1)
+        self.rowptr = torch.as_tensor(np.asarray(rowptr, dtype=np.int64) if isinstance(rowptr, np.ndarray) else rowptr,
+                                      dtype=torch.int64).to(self.device).contiguous()
+        self.col = torch.as_tensor(np.asarray(col, dtype=np.int32) if isinstance(col, np.ndarray) else col,
+                                   dtype=torch.int32).to(self.device).contiguous()
+        self.val = _values_tensor(torch, val, dtype, self.device)
+        self.d = int(self.rowptr.numel() - 1)
+        self.nnz = int(self.col.numel())
+        self.dtype = dtype
+        self.kind = kind
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = B.cld_create_batch(self.blk_rows, self.nnz, self.rowptr, self.col, self.val, _DTYPES[dtype],
+                                    _KINDS[kind], self.stream.cuda_stream)
+        self.ws = None
+        self.ws_bytes = 0
+
+    def set_intervals(self, a, b):
+        B.cld_batch_set_intervals(self.h, a, b)
+
+    def auto_intervals(self):
+        self.reserve(0, 1)
+        return B.cld_batch_auto_intervals(self.h, self.nb)
+
+    def set_tile_rows(self, rows: int):
+        B.cld_batch_set_tile_rows(self.h, rows)
+
+    def estimate(self, n: int, M: int, seed: int = 0):
+        self.reserve(n, M)
+        g, se = B.cld_batch_estimate(self.h, self.nb, n, M, seed)
+        return {"logdet": g, "stderr": se}
 
 
 def logdet(rowptr, col, val, n: int, M: int, seed: int = 0, interval=None, dtype: str = "f32",

@@ -38,35 +38,34 @@ template <int LPR>
 __device__ __forceinline__ void adj_reduce_scatter4(float (&dt)[4], int lig, unsigned gmask, float& sa, float& sb) {
     sa = 0.f;
     sb = 0.f;
-    if (LPR == 1) return;
-    if (LPR == 2) {
+    if constexpr (LPR == 2) {
         // lane 0 keeps entries 0,1; lane 1 keeps 2,3
         const bool hi = lig & 1;
         const float s0 = hi ? dt[0] : dt[2], s1 = hi ? dt[1] : dt[3];
         const float r0 = __shfl_xor_sync(gmask, s0, 1, LPR), r1 = __shfl_xor_sync(gmask, s1, 1, LPR);
         sa = (hi ? dt[2] : dt[0]) + r0;
         sb = (hi ? dt[3] : dt[1]) + r1;
-        return;
-    }
-    // fold the upper lanes until 8 (or 4) remain
+    } else if constexpr (LPR >= 4) {
+        // fold the upper lanes until 8 (or 4) remain
 #pragma unroll
-    for (int off = LPR / 2; off >= 8; off >>= 1) {
+        for (int off = LPR / 2; off >= 8; off >>= 1) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(gmask, dt[u], off, LPR);
+            for (int u = 0; u < 4; ++u) dt[u] += __shfl_xor_sync(gmask, dt[u], off, LPR);
+        }
+        constexpr int W = LPR >= 8 ? 8 : 4;
+        // stage A over xor W/2: keep entries {0,1} or {2,3}
+        const bool ha = (lig & (W / 2)) != 0;
+        const float s0 = ha ? dt[0] : dt[2], s1 = ha ? dt[1] : dt[3];
+        float k0 = (ha ? dt[2] : dt[0]) + __shfl_xor_sync(gmask, s0, W / 2, LPR);
+        float k1 = (ha ? dt[3] : dt[1]) + __shfl_xor_sync(gmask, s1, W / 2, LPR);
+        // stage B over xor W/4: keep one entry
+        const bool hb = (lig & (W / 4)) != 0;
+        const float snd = hb ? k0 : k1;
+        float kk = (hb ? k1 : k0) + __shfl_xor_sync(gmask, snd, W / 4, LPR);
+        // stage C (W = 8 only): finish over xor 1
+        if (W == 8) kk += __shfl_xor_sync(gmask, kk, 1, LPR);
+        sa = kk;
     }
-    constexpr int W = LPR >= 8 ? 8 : 4;
-    // stage A over xor W/2: keep entries {0,1} or {2,3}
-    const bool ha = (lig & (W / 2)) != 0;
-    const float s0 = ha ? dt[0] : dt[2], s1 = ha ? dt[1] : dt[3];
-    float k0 = (ha ? dt[2] : dt[0]) + __shfl_xor_sync(gmask, s0, W / 2, LPR);
-    float k1 = (ha ? dt[3] : dt[1]) + __shfl_xor_sync(gmask, s1, W / 2, LPR);
-    // stage B over xor W/4: keep one entry
-    const bool hb = (lig & (W / 4)) != 0;
-    const float snd = hb ? k0 : k1;
-    float kk = (hb ? k1 : k0) + __shfl_xor_sync(gmask, snd, W / 4, LPR);
-    // stage C (W = 8 only): finish over xor 1
-    if (W == 8) kk += __shfl_xor_sync(gmask, kk, 1, LPR);
-    sa = kk;
 }
 
 // MODE 0: lambda_{i+1} = 0 (i = n): lambda_i = c_i v; no gather, no H term.

@@ -173,10 +173,11 @@ cudaError_t launch_coeffs(int n, const Params* prm, double* coeffs, double* coef
     return cudaGetLastError();
 }
 
-__global__ void finalize_kernel(int n, int M, int64_t d, int general, const Params* prm,
-                                double* __restrict__ T, double* __restrict__ coeffs,
-                                double* __restrict__ scratch, double* __restrict__ gamma_p,
-                                Result* res) {
+// One problem's final sums (one CTA): coefficients, t_0 = d, Gamma_p, Gamma,
+// stderr and the spectrum check into *res.
+__device__ void finalize_one(int n, int M, int64_t d, int general, const Params* prm,
+                             double* __restrict__ T, double* __restrict__ coeffs,
+                             double* __restrict__ scratch, double* __restrict__ gamma_p, Result* res) {
     __shared__ double sh[kThreads];
     chebyshev_coefficients(n, prm->a, prm->b, coeffs, scratch);
     for (int p = threadIdx.x; p < M; p += blockDim.x) T[p] = (double)d;
@@ -211,6 +212,30 @@ __global__ void finalize_kernel(int n, int M, int64_t d, int general, const Para
         res->max_ratio = rmax;
         res->spectrum_bad = (nbad > 0.0 || !(rmax <= 1.0 + 1e-3)) ? 1 : 0;
     }
+}
+
+__global__ void finalize_kernel(int n, int M, int64_t d, int general, const Params* prm,
+                                double* __restrict__ T, double* __restrict__ coeffs,
+                                double* __restrict__ scratch, double* __restrict__ gamma_p,
+                                Result* res) {
+    finalize_one(n, M, d, general, prm, T, coeffs, scratch, gamma_p, res);
+}
+
+// Batched final sums: CTA b finalises block b (its own interval, d_b rows).
+__global__ void finalize_batch_kernel(int n, int M, const int64_t* __restrict__ blk_rows, int general,
+                                      const Params* prm, double* __restrict__ T, double* __restrict__ coeffs,
+                                      double* __restrict__ scratch, double* __restrict__ gamma_p, Result* res) {
+    const int b = blockIdx.x;
+    const int64_t db = blk_rows[b + 1] - blk_rows[b];
+    finalize_one(n, M, db, general, prm + b, T + (size_t)b * (n + 1) * M, coeffs + (size_t)b * (n + 1),
+                 scratch + (size_t)b * 5 * (n + 1), gamma_p + (size_t)b * M, res + b);
+}
+
+cudaError_t launch_finalize_batch(int nb, int n, int M, const int64_t* blk_rows, int general, const Params* prm,
+                                  double* T, double* coeffs, double* coef_scratch, double* gamma_p, Result* res,
+                                  cudaStream_t s) {
+    finalize_batch_kernel<<<nb, kThreads, 0, s>>>(n, M, blk_rows, general, prm, T, coeffs, coef_scratch, gamma_p, res);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_finalize(int n, int M, int64_t d, int general, const Params* prm, double* T,

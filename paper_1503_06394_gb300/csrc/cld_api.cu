@@ -78,6 +78,22 @@ struct cld_ctx {
 
     int impl = 1;  // recurrence-step inner loop (see step_kernel.cuh)
 
+    // batch (nb > 0): block-diagonal super matrix, blocks [blk_rows[b], blk_rows[b+1])
+    int nb = 0;
+    std::vector<int64_t> blk_rows;
+    int tile_rows = 1024;
+    int64_t max_tiles = 0;
+    std::vector<Tile> tiles;
+    std::vector<int64_t> tile_start;
+    std::vector<double> ba, bb;  // per-block intervals
+    bool have_bintervals = false;
+
+    // CUDA graph of one estimate (set-seed stays outside the graph)
+    bool use_graph = false;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    long long gkey[6] = {0, 0, 0, 0, 0, 0};
+
     int last_n = -1, last_M = -1;
     bool profiling = false;
     std::vector<cudaEvent_t> ev;
@@ -91,6 +107,7 @@ struct Layout {
     size_t params, result, flags, rowptrT, colT, valT, tscratch, run;  // fixed part
     size_t coeffs, coef_scratch, T, gamma_p, tpart, gpart, vbits, W[3], Y, lanczos, total;
     size_t Wall, lam[3], H;  // gradient: w_1..w_n, the adjoint ring, per-entry sums
+    size_t blk_rows, tile_start, tiles, bprm, ab, bres;  // batches
     int panel, nw, grid, ggrid;
 };
 
@@ -128,6 +145,14 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
         L.valT = o; o += align_up((size_t)h->nnz * value_size(h->dtype));
         L.tscratch = o; o += align_up((size_t)(h->d + 1) * 8);
     }
+    const int nprob = h->nb > 0 ? h->nb : 1;
+    if (h->nb > 0) {
+        L.blk_rows = o; o += align_up((size_t)(h->nb + 1) * 8);
+        L.tile_start = o; o += align_up((size_t)(h->nb + 1) * 8);
+        L.tiles = o; o += align_up((size_t)h->max_tiles * sizeof(Tile));
+        L.bprm = o; o += align_up((size_t)h->nb * sizeof(Params));
+        L.ab = o; o += align_up((size_t)h->nb * 2 * 8);
+    }
     L.run = o;
     const int nn = n > 0 ? n : 0;
     const int MM = M > 0 ? M : 1;
@@ -135,11 +160,13 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
     L.nw = sign_words(L.panel);
     L.grid = step_grid(h, L.panel);
     L.ggrid = stream_grid(h);
-    L.coeffs = o; o += align_up((size_t)(nn + 1) * 8);
-    L.coef_scratch = o; o += align_up((size_t)5 * (nn + 1) * 8);
-    L.T = o; o += align_up((size_t)(nn + 1) * MM * 8);
-    L.gamma_p = o; o += align_up((size_t)MM * 8);
-    L.tpart = o; o += align_up((size_t)(nn > 0 ? nn : 1) * L.grid * L.panel * 8);
+    L.coeffs = o; o += align_up((size_t)nprob * (nn + 1) * 8);
+    L.coef_scratch = o; o += align_up((size_t)nprob * 5 * (nn + 1) * 8);
+    L.T = o; o += align_up((size_t)nprob * (nn + 1) * MM * 8);
+    L.gamma_p = o; o += align_up((size_t)nprob * MM * 8);
+    L.bres = o; o += align_up((size_t)nprob * sizeof(Result));
+    const int64_t tslots = h->nb > 0 ? h->max_tiles : L.grid;
+    L.tpart = o; o += align_up((size_t)(nn > 0 ? nn : 1) * tslots * L.panel * 8);
     L.gpart = o; o += align_up((size_t)4 * L.ggrid * 8 + 64);  // 4 doubles per CTA (general bounds)
     L.vbits = o; o += align_up((size_t)h->d * L.nw * 4);
     const size_t wb = align_up((size_t)h->d * L.panel * 4);
@@ -163,140 +190,6 @@ static T* at(cld_ctx* h, size_t off) { return reinterpret_cast<T*>(h->ws + off);
 
 static cld_status check_handle(cld_handle h) {
     if (!h) return fail(CLD_ERR_INVALID, "NULL handle");
-    return CLD_OK;
-}
-
-extern "C" {
-
-const char* cld_last_error(void) { return g_err.c_str(); }
-const char* cld_version(void) { return "libcld 0.1 (sm_103a)"; }
-
-cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t* rowptr,
-                          const int32_t* col, const void* val, cld_dtype val_dtype,
-                          cld_kind kind, void* stream) {
-    if (!out) return fail(CLD_ERR_INVALID, "out is NULL");
-    *out = nullptr;
-    if (d < 0 || nnz < 0) return fail(CLD_ERR_INVALID, "negative size (d=%lld, nnz=%lld)",
-                                      (long long)d, (long long)nnz);
-    if (d >= (int64_t)INT32_MAX) return fail(CLD_ERR_INVALID, "d must be < 2^31 (int32 columns)");
-    if (!rowptr || (nnz > 0 && (!col || !val)))
-        return fail(CLD_ERR_INVALID, "NULL CSR array");
-    if (val_dtype != CLD_F32 && val_dtype != CLD_BF16 && val_dtype != CLD_F64)
-        return fail(CLD_ERR_INVALID, "unknown value dtype %d", (int)val_dtype);
-    if (kind != CLD_SPD && kind != CLD_GENERAL) return fail(CLD_ERR_INVALID, "unknown kind %d", (int)kind);
-    cld_ctx* h = new (std::nothrow) cld_ctx;
-    if (!h) return fail(CLD_ERR_NOMEM, "host allocation failed");
-    h->d = d; h->nnz = nnz; h->rowptr = rowptr; h->col = col; h->val = val;
-    h->dtype = val_dtype; h->kind = kind; h->stream = (cudaStream_t)stream;
-    // Default inner loop: cooperative 4-entry chunks pay off once rows hold
-    // about 8 or more stored entries (measured on GB300: random SPD with 11
-    // entries per row 3.22 vs 3.27 ms per step; 5-point grid 0.32 vs 0.22 ms).
-    h->impl = (d > 0 && nnz >= 8 * d) ? 2 : 0;
-    if (cudaGetDevice(&h->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
-        delete h;
-        return fail(CLD_ERR_CUDA, "no CUDA device");
-    }
-    *out = h;
-    return CLD_OK;
-}
-
-void cld_destroy(cld_handle h) {
-    if (!h) return;
-    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-    delete h;
-}
-
-cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes) {
-    if (check_handle(h)) return CLD_ERR_INVALID;
-    if (!bytes || n < 0 || M < 1) return fail(CLD_ERR_INVALID, "bad arguments (n=%d, M=%d)", n, M);
-    *bytes = make_layout(h, n, M, with_grad).total;
-    return CLD_OK;
-}
-
-cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes) {
-    if (check_handle(h)) return CLD_ERR_INVALID;
-    if (!dev_ptr) return fail(CLD_ERR_INVALID, "NULL workspace");
-    if (((uintptr_t)dev_ptr) % 256) return fail(CLD_ERR_INVALID, "workspace not 256-byte aligned");
-    const Layout L = make_layout(h, 0, 1, 0);
-    if (bytes < L.run) return fail(CLD_ERR_NOMEM, "workspace smaller than the fixed header");
-    h->ws = static_cast<char*>(dev_ptr);
-    h->ws_bytes = bytes;
-    h->ready = false;
-    uint32_t* flags = at<uint32_t>(h, L.flags);
-    CUDA_TRY(cudaMemsetAsync(flags, 0, 256, h->stream));
-    if (h->d > 0)
-        CUDA_TRY(launch_validate_csr(h->d, h->nnz, h->rowptr, h->col, h->val, (int)h->dtype, flags,
-                                     stream_grid(h), h->stream));
-    uint32_t f = 0;
-    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (f & 1u) return fail(CLD_ERR_INVALID, "row pointers must start at 0, end at nnz and not decrease");
-    if (f & 2u) return fail(CLD_ERR_INVALID, "column index out of range [0, d)");
-    if (f & 4u) return fail(CLD_ERR_INVALID, "non-finite stored value");
-    if (h->kind == CLD_GENERAL && h->d > 0) {
-        CUDA_TRY(launch_transpose(h->d, h->nnz, h->rowptr, h->col, h->val, value_size(h->dtype),
-                                  at<int64_t>(h, L.rowptrT), at<int32_t>(h, L.colT), at<void>(h, L.valT),
-                                  at<int64_t>(h, L.tscratch), stream_grid(h), h->stream));
-        CUDA_TRY(cudaStreamSynchronize(h->stream));
-    }
-    if (h->have_interval)
-        CUDA_TRY(launch_set_params(at<Params>(h, L.params), h->a, h->b, h->stream));
-    h->ready = true;
-    return CLD_OK;
-}
-
-cld_status cld_set_interval(cld_handle h, double a, double b) {
-    if (check_handle(h)) return CLD_ERR_INVALID;
-    if (!(a > 0.0) || !(a < b) || !isfinite(a) || !isfinite(b))
-        return fail(CLD_ERR_INTERVAL, "interval must satisfy 0 < a < b (got [%g, %g])", a, b);
-    h->a = a;
-    h->b = b;
-    h->have_interval = true;
-    if (h->ws) {
-        const Layout L = make_layout(h, 0, 1, 0);
-        CUDA_TRY(launch_set_params(at<Params>(h, L.params), a, b, h->stream));
-    }
-    return CLD_OK;
-}
-
-cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a_out, double* b_out) {
-    if (check_handle(h)) return CLD_ERR_INVALID;
-    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
-    if (h->d == 0) return fail(CLD_ERR_INTERVAL, "empty matrix has no spectrum");
-    if (lanczos_iters < 0 || lanczos_iters > 4000) return fail(CLD_ERR_INVALID, "lanczos_iters in [0, 4000]");
-    const Layout L = make_layout(h, 0, 1, 0);
-    if (lanczos_iters > 0 && h->ws_bytes < make_layout(h, 0, 1, 0).total)
-        return fail(CLD_ERR_NOMEM, "workspace too small for the Lanczos pass");
-    Params* prm = at<Params>(h, L.params);
-    uint32_t* flags = at<uint32_t>(h, L.flags);
-    CUDA_TRY(cudaMemsetAsync(flags, 0, 4, h->stream));
-    if (h->kind == CLD_SPD) {
-        CUDA_TRY(launch_gershgorin(h->d, h->rowptr, h->col, h->val, (int)h->dtype, at<double>(h, L.gpart),
-                                   L.ggrid, prm, flags, h->stream));
-        if (lanczos_iters > 0)
-            CUDA_TRY(launch_lanczos(h->d, h->rowptr, h->col, h->val, (int)h->dtype, lanczos_iters,
-                                    at<double>(h, L.lanczos), at<double>(h, L.lanczos) + 5 * h->d,
-                                    L.ggrid, prm, flags, h->stream));
-    } else {
-        CUDA_TRY(launch_general_bounds(h->d, h->rowptr, h->col, h->val, at<int64_t>(h, L.rowptrT),
-                                       at<int32_t>(h, L.colT), at<void>(h, L.valT), (int)h->dtype,
-                                       at<double>(h, L.gpart), L.ggrid, prm, flags, h->stream));
-    }
-    Params p{};
-    uint32_t f = 0;
-    CUDA_TRY(cudaMemcpyAsync(&p, prm, sizeof(Params), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (a_out) *a_out = p.a;
-    if (b_out) *b_out = p.b;
-    if ((f & 0x100u) || !p.interval_ok) {
-        h->have_interval = false;
-        return fail(CLD_ERR_INTERVAL, "computed interval [%g, %g] is not a valid 0 < a < b", p.a, p.b);
-    }
-    h->a = p.a;
-    h->b = p.b;
-    h->have_interval = true;
     return CLD_OK;
 }
 
@@ -375,14 +268,16 @@ static cld_status ensure_events(cld_ctx* h, int M) {
     return CLD_OK;
 }
 
-static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed) {
+static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed, bool with_seed) {
     Params* prm = at<Params>(h, L.params);
     int launches = 0, step_launches = 0;
     const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
     cld_status st = ensure_events(h, M);
     if (st != CLD_OK) return st;
-    CUDA_TRY(launch_set_seed(prm, seed, h->stream));
-    ++launches;
+    if (with_seed) {
+        CUDA_TRY(launch_set_seed(prm, seed, h->stream));
+        ++launches;
+    }
     for (int pk = 0; pk < npanels; ++pk) {
         st = enqueue_panel_forward(h, L, n, M, pk, false, &launches, &step_launches);
         if (st != CLD_OK) return st;
@@ -393,6 +288,192 @@ static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, ui
     ++launches;
     h->last_total_launches = launches;
     h->last_step_launches = step_launches;
+    return CLD_OK;
+}
+
+
+// ---------------------------------------------------------------- batches
+static void build_tiles(cld_ctx* h) {
+    h->tiles.clear();
+    h->tile_start.assign((size_t)h->nb + 1, 0);
+    for (int b = 0; b < h->nb; ++b) {
+        h->tile_start[b] = (int64_t)h->tiles.size();
+        for (int64_t r = h->blk_rows[b]; r < h->blk_rows[b + 1]; r += h->tile_rows) {
+            Tile t;
+            t.lo = r;
+            t.hi = r + h->tile_rows < h->blk_rows[b + 1] ? r + h->tile_rows : h->blk_rows[b + 1];
+            t.blk = b;
+            t.pad = 0;
+            h->tiles.push_back(t);
+        }
+    }
+    h->tile_start[h->nb] = (int64_t)h->tiles.size();
+}
+
+static cld_status upload_batch_tables(cld_ctx* h, const Layout& L) {
+    CUDA_TRY(cudaMemcpyAsync(at<int64_t>(h, L.blk_rows), h->blk_rows.data(), sizeof(int64_t) * (h->nb + 1),
+                             cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(at<int64_t>(h, L.tile_start), h->tile_start.data(), sizeof(int64_t) * (h->nb + 1),
+                             cudaMemcpyHostToDevice, h->stream));
+    if (!h->tiles.empty())
+        CUDA_TRY(cudaMemcpyAsync(at<Tile>(h, L.tiles), h->tiles.data(), sizeof(Tile) * h->tiles.size(),
+                                 cudaMemcpyHostToDevice, h->stream));
+    return CLD_OK;
+}
+
+static BatchAuxArgs batch_aux_args(cld_ctx* h, const Layout& L) {
+    BatchAuxArgs x{};
+    x.bprm = at<Params>(h, L.bprm);
+    x.ab = at<double>(h, L.ab);
+    x.tiles = at<Tile>(h, L.tiles);
+    x.ntiles = (int64_t)h->tiles.size();
+    x.tile_start = at<int64_t>(h, L.tile_start);
+    x.blk_rows = at<int64_t>(h, L.blk_rows);
+    x.nw = L.nw;
+    x.vbits = at<uint32_t>(h, L.vbits);
+    x.dtype = (int)h->dtype;
+    x.rowptr = h->rowptr;
+    x.col = h->col;
+    x.val = h->val;
+    if (h->kind == CLD_GENERAL) {
+        x.rowptrT = at<int64_t>(h, L.rowptrT);
+        x.colT = at<int32_t>(h, L.colT);
+        x.valT = at<void>(h, L.valT);
+    }
+    x.flags = at<uint32_t>(h, L.flags);
+    return x;
+}
+
+static cld_status enqueue_batch(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed, bool with_seed) {
+    BatchAuxArgs x = batch_aux_args(h, L);
+    const int nb = h->nb;
+    int launches = 0;
+    if (with_seed) {
+        x.seed = seed;
+        CUDA_TRY(launch_batch_aux(0, nb, 1, h->stream, x));
+        ++launches;
+    }
+    const bool general = h->kind == CLD_GENERAL;
+    const int64_t ntiles = (int64_t)h->tiles.size();
+    const int grid = (int)(ntiles < L.grid ? (ntiles > 0 ? ntiles : 1) : L.grid);
+    double* tpart = at<double>(h, L.tpart);
+    float* W[3] = {at<float>(h, L.W[0]), at<float>(h, L.W[1]), at<float>(h, L.W[2])};
+    float* Y = general ? at<float>(h, L.Y) : nullptr;
+    const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+    for (int pk = 0; pk < npanels; ++pk) {
+        const int pbase = pk * kMaxPanel;
+        const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
+        x.panel = (uint32_t)pk;
+        CUDA_TRY(launch_batch_aux(2, nb, L.ggrid, h->stream, x));
+        ++launches;
+        BatchStepArgs bs{};
+        bs.tiles = x.tiles;
+        bs.ntiles = ntiles;
+        bs.bprm = x.bprm;
+        bs.s.d = h->d;
+        bs.s.vbits = x.vbits;
+        bs.s.mreal = mreal;
+        bs.s.impl = h->impl;
+        for (int j = 0; j < n; ++j) {
+            const float* wj = j >= 1 ? W[j % 3] : nullptr;
+            const float* wjm = j >= 2 ? W[(j - 1) % 3] : nullptr;
+            float* wout = W[(j + 1) % 3];
+            bs.tpart = tpart + (size_t)j * ntiles * L.panel;
+            StepKind kind;
+            if (general) {
+                StepArgs p{};
+                p.d = h->d;
+                p.rowptr = h->rowptr; p.col = h->col; p.val = h->val;
+                p.vbits = x.vbits; p.mreal = mreal; p.impl = h->impl;
+                p.x = wj; p.out = Y;
+                CUDA_TRY(launch_step(L.panel, (int)h->dtype, j == 0 ? kProdBits : kProdFloat, L.grid, h->stream, p));
+                ++launches;
+                bs.s.rowptr = x.rowptrT; bs.s.col = x.colT; bs.s.val = x.valT;
+                bs.s.x = Y; bs.s.own = wj; bs.s.wprev = wjm; bs.s.out = wout;
+                kind = j == 0 ? kStepFirstFromFloat : j == 1 ? kStepSecond : kStepGeneral;
+            } else {
+                bs.s.rowptr = h->rowptr; bs.s.col = h->col; bs.s.val = h->val;
+                bs.s.x = wj; bs.s.own = wj; bs.s.wprev = wjm; bs.s.out = wout;
+                kind = j == 0 ? kStepFirst : j == 1 ? kStepSecond : kStepGeneral;
+            }
+            CUDA_TRY(launch_batch_step(L.panel, (int)h->dtype, kind, grid, h->stream, bs));
+            ++launches;
+        }
+        if (n > 0) {
+            x.tpart = tpart;
+            x.panel_width = L.panel;
+            x.mreal = mreal;
+            x.n = n;
+            x.M = M;
+            x.pbase = pbase;
+            x.nsteps = n;
+            x.T = at<double>(h, L.T);
+            CUDA_TRY(launch_batch_aux(3, nb, 1, h->stream, x));
+            ++launches;
+        }
+    }
+    CUDA_TRY(launch_finalize_batch(nb, n, M, x.blk_rows, general ? 1 : 0, x.bprm, at<double>(h, L.T),
+                                   at<double>(h, L.coeffs), at<double>(h, L.coef_scratch), at<double>(h, L.gamma_p),
+                                   at<Result>(h, L.bres), h->stream));
+    ++launches;
+    h->last_total_launches = launches;
+    h->last_step_launches = 0;
+    return CLD_OK;
+}
+
+// Uploads the per-block intervals (a_b, b_b pairs) and sets each block's
+// parameters on the device.
+static cld_status apply_bintervals(cld_ctx* h, const Layout& L) {
+    std::vector<double> ab((size_t)2 * h->nb);
+    for (int b = 0; b < h->nb; ++b) {
+        ab[2 * b] = h->ba[b];
+        ab[2 * b + 1] = h->bb[b];
+    }
+    CUDA_TRY(cudaMemcpyAsync(at<double>(h, L.ab), ab.data(), sizeof(double) * ab.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+    BatchAuxArgs x = batch_aux_args(h, L);
+    CUDA_TRY(launch_batch_aux(1, h->nb, 1, h->stream, x));
+    return CLD_OK;
+}
+
+// Runs enqueue(with_seed = false) through a CUDA graph captured once per
+// (call kind, n, M, variant, workspace, tile size); the seed is set by a
+// separate launch before the graph.
+template <typename F>
+static cld_status run_graph(cld_ctx* h, long long kind, int n, int M, F&& enqueue) {
+    const long long key[6] = {kind, n, M, h->impl, (long long)(uintptr_t)h->ws, h->tile_rows};
+    if (!h->gexec || memcmp(key, h->gkey, sizeof(key)) != 0) {
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        // order the capture after work already queued on the user's stream
+        cudaStream_t user = h->stream;
+        const bool prof = h->profiling;
+        h->profiling = false;
+        h->stream = h->cap_stream;
+        cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+        cld_status st = e == cudaSuccess ? enqueue() : fail(CLD_ERR_CUDA, "cudaStreamBeginCapture: %s",
+                                                            cudaGetErrorString(e));
+        cudaGraph_t g = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->cap_stream, &g);
+        h->stream = user;
+        h->profiling = prof;
+        if (st != CLD_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e2 != cudaSuccess) return fail(CLD_ERR_CUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e2));
+        e = cudaGraphInstantiate(&h->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->gexec = nullptr;
+            return fail(CLD_ERR_CUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+        }
+        memcpy(h->gkey, key, sizeof(key));
+    }
+    CUDA_TRY(cudaGraphLaunch(h->gexec, h->stream));
     return CLD_OK;
 }
 
@@ -422,12 +503,163 @@ static cld_status read_result(cld_ctx* h, const Layout& L, int n, int M, double*
     return CLD_OK;
 }
 
+extern "C" {
+
+const char* cld_last_error(void) { return g_err.c_str(); }
+const char* cld_version(void) { return "libcld 0.1 (sm_103a)"; }
+
+cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t* rowptr,
+                          const int32_t* col, const void* val, cld_dtype val_dtype,
+                          cld_kind kind, void* stream) {
+    if (!out) return fail(CLD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (d < 0 || nnz < 0) return fail(CLD_ERR_INVALID, "negative size (d=%lld, nnz=%lld)",
+                                      (long long)d, (long long)nnz);
+    if (d >= (int64_t)INT32_MAX) return fail(CLD_ERR_INVALID, "d must be < 2^31 (int32 columns)");
+    if (!rowptr || (nnz > 0 && (!col || !val)))
+        return fail(CLD_ERR_INVALID, "NULL CSR array");
+    if (val_dtype != CLD_F32 && val_dtype != CLD_BF16 && val_dtype != CLD_F64)
+        return fail(CLD_ERR_INVALID, "unknown value dtype %d", (int)val_dtype);
+    if (kind != CLD_SPD && kind != CLD_GENERAL) return fail(CLD_ERR_INVALID, "unknown kind %d", (int)kind);
+    cld_ctx* h = new (std::nothrow) cld_ctx;
+    if (!h) return fail(CLD_ERR_NOMEM, "host allocation failed");
+    h->d = d; h->nnz = nnz; h->rowptr = rowptr; h->col = col; h->val = val;
+    h->dtype = val_dtype; h->kind = kind; h->stream = (cudaStream_t)stream;
+    // Default inner loop: cooperative 4-entry chunks pay off once rows hold
+    // about 8 or more stored entries (measured on GB300: random SPD with 11
+    // entries per row 3.22 vs 3.27 ms per step; 5-point grid 0.32 vs 0.22 ms).
+    h->impl = (d > 0 && nnz >= 8 * d) ? 2 : 0;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return fail(CLD_ERR_CUDA, "no CUDA device");
+    }
+    *out = h;
+    return CLD_OK;
+}
+
+void cld_destroy(cld_handle h) {
+    if (!h) return;
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    delete h;
+}
+
+cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!bytes || n < 0 || M < 1) return fail(CLD_ERR_INVALID, "bad arguments (n=%d, M=%d)", n, M);
+    *bytes = make_layout(h, n, M, with_grad).total;
+    return CLD_OK;
+}
+
+cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!dev_ptr) return fail(CLD_ERR_INVALID, "NULL workspace");
+    if (((uintptr_t)dev_ptr) % 256) return fail(CLD_ERR_INVALID, "workspace not 256-byte aligned");
+    const Layout L = make_layout(h, 0, 1, 0);
+    if (bytes < L.run) return fail(CLD_ERR_NOMEM, "workspace smaller than the fixed header");
+    h->ws = static_cast<char*>(dev_ptr);
+    h->ws_bytes = bytes;
+    h->ready = false;
+    uint32_t* flags = at<uint32_t>(h, L.flags);
+    CUDA_TRY(cudaMemsetAsync(flags, 0, 256, h->stream));
+    if (h->d > 0)
+        CUDA_TRY(launch_validate_csr(h->d, h->nnz, h->rowptr, h->col, h->val, (int)h->dtype, flags,
+                                     stream_grid(h), h->stream));
+    uint32_t f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (f & 1u) return fail(CLD_ERR_INVALID, "row pointers must start at 0, end at nnz and not decrease");
+    if (f & 2u) return fail(CLD_ERR_INVALID, "column index out of range [0, d)");
+    if (f & 4u) return fail(CLD_ERR_INVALID, "non-finite stored value");
+    if (h->nb > 0) {
+        cld_status st = upload_batch_tables(h, L);
+        if (st != CLD_OK) return st;
+        BatchAuxArgs x = batch_aux_args(h, L);
+        if (h->d > 0) CUDA_TRY(launch_batch_aux(6, h->nb, stream_grid(h), h->stream, x));
+        CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+        if (f & 8u) return fail(CLD_ERR_INVALID, "batch matrix is not block diagonal (column outside its block)");
+        if (h->have_bintervals) {
+            st = apply_bintervals(h, L);
+            if (st != CLD_OK) return st;
+        }
+    }
+    if (h->kind == CLD_GENERAL && h->d > 0) {
+        CUDA_TRY(launch_transpose(h->d, h->nnz, h->rowptr, h->col, h->val, value_size(h->dtype),
+                                  at<int64_t>(h, L.rowptrT), at<int32_t>(h, L.colT), at<void>(h, L.valT),
+                                  at<int64_t>(h, L.tscratch), stream_grid(h), h->stream));
+        CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    if (h->have_interval)
+        CUDA_TRY(launch_set_params(at<Params>(h, L.params), h->a, h->b, h->stream));
+    h->ready = true;
+    return CLD_OK;
+}
+
+cld_status cld_set_interval(cld_handle h, double a, double b) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!(a > 0.0) || !(a < b) || !isfinite(a) || !isfinite(b))
+        return fail(CLD_ERR_INTERVAL, "interval must satisfy 0 < a < b (got [%g, %g])", a, b);
+    h->a = a;
+    h->b = b;
+    h->have_interval = true;
+    if (h->ws) {
+        const Layout L = make_layout(h, 0, 1, 0);
+        CUDA_TRY(launch_set_params(at<Params>(h, L.params), a, b, h->stream));
+    }
+    return CLD_OK;
+}
+
+cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a_out, double* b_out) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
+    if (h->nb > 0) return fail(CLD_ERR_INVALID, "batch handle: use cld_batch_auto_intervals");
+    if (h->d == 0) return fail(CLD_ERR_INTERVAL, "empty matrix has no spectrum");
+    if (lanczos_iters < 0 || lanczos_iters > 4000) return fail(CLD_ERR_INVALID, "lanczos_iters in [0, 4000]");
+    const Layout L = make_layout(h, 0, 1, 0);
+    if (lanczos_iters > 0 && h->ws_bytes < make_layout(h, 0, 1, 0).total)
+        return fail(CLD_ERR_NOMEM, "workspace too small for the Lanczos pass");
+    Params* prm = at<Params>(h, L.params);
+    uint32_t* flags = at<uint32_t>(h, L.flags);
+    CUDA_TRY(cudaMemsetAsync(flags, 0, 4, h->stream));
+    if (h->kind == CLD_SPD) {
+        CUDA_TRY(launch_gershgorin(h->d, h->rowptr, h->col, h->val, (int)h->dtype, at<double>(h, L.gpart),
+                                   L.ggrid, prm, flags, h->stream));
+        if (lanczos_iters > 0)
+            CUDA_TRY(launch_lanczos(h->d, h->rowptr, h->col, h->val, (int)h->dtype, lanczos_iters,
+                                    at<double>(h, L.lanczos), at<double>(h, L.lanczos) + 5 * h->d,
+                                    L.ggrid, prm, flags, h->stream));
+    } else {
+        CUDA_TRY(launch_general_bounds(h->d, h->rowptr, h->col, h->val, at<int64_t>(h, L.rowptrT),
+                                       at<int32_t>(h, L.colT), at<void>(h, L.valT), (int)h->dtype,
+                                       at<double>(h, L.gpart), L.ggrid, prm, flags, h->stream));
+    }
+    Params p{};
+    uint32_t f = 0;
+    CUDA_TRY(cudaMemcpyAsync(&p, prm, sizeof(Params), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (a_out) *a_out = p.a;
+    if (b_out) *b_out = p.b;
+    if ((f & 0x100u) || !p.interval_ok) {
+        h->have_interval = false;
+        return fail(CLD_ERR_INTERVAL, "computed interval [%g, %g] is not a valid 0 < a < b", p.a, p.b);
+    }
+    h->a = p.a;
+    h->b = p.b;
+    h->have_interval = true;
+    return CLD_OK;
+}
+
 cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
                         double* stderr_out, double* moments_out) {
     if (check_handle(h)) return CLD_ERR_INVALID;
     if (n < 0 || M < 1) return fail(CLD_ERR_INVALID, "need n >= 0 and M >= 1 (n=%d, M=%d)", n, M);
     if (n > 100000) return fail(CLD_ERR_INVALID, "degree n > 100000 is not supported");
     if (!logdet_out) return fail(CLD_ERR_INVALID, "logdet_out is NULL");
+    if (h->nb > 0) return fail(CLD_ERR_INVALID, "batch handle: use cld_batch_estimate");
     if (!h->have_interval) return fail(CLD_ERR_INTERVAL, "no spectral interval set");
     if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
     const Layout L = make_layout(h, n, M, 0);
@@ -441,7 +673,14 @@ cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logde
         h->last_total_launches = h->last_step_launches = 0;
         return CLD_OK;
     }
-    cld_status st = enqueue_estimate(h, L, n, M, seed);
+    cld_status st;
+    if (h->use_graph) {
+        CUDA_TRY(launch_set_seed(at<Params>(h, L.params), seed, h->stream));
+        st = run_graph(h, 1, n, M, [&]() { return enqueue_estimate(h, L, n, M, seed, false); });
+        ++h->last_total_launches;
+    } else {
+        st = enqueue_estimate(h, L, n, M, seed, true);
+    }
     if (st != CLD_OK) return st;
     Result r{};
     st = read_result(h, L, n, M, logdet_out, stderr_out, moments_out, &r);
@@ -469,7 +708,8 @@ cld_status cld_last_details(cld_handle h, double* coeffs_out, double* gamma_p_ou
 
 cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out, float* dvalues_dev) {
     if (check_handle(h)) return CLD_ERR_INVALID;
-    if (h->kind != CLD_SPD) return fail(CLD_ERR_UNSUPPORTED, "cld_grad supports CLD_SPD matrices only");
+    if (h->kind != CLD_SPD || h->nb > 0)
+        return fail(CLD_ERR_UNSUPPORTED, "cld_grad supports single CLD_SPD matrices only");
     if (n < 0 || M < 1 || n > 100000) return fail(CLD_ERR_INVALID, "need 0 <= n <= 100000 and M >= 1");
     if (!logdet_out) return fail(CLD_ERR_INVALID, "logdet_out is NULL");
     if (!dvalues_dev && h->nnz > 0) return fail(CLD_ERR_INVALID, "dvalues_dev is NULL");
@@ -601,6 +841,129 @@ cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* rowptr_hos
     return st;
 }
 
+
+cld_status cld_create_batch(cld_handle* out, int nb, const int64_t* blk_rows, int64_t nnz, const int64_t* rowptr,
+                            const int32_t* col, const void* val, cld_dtype val_dtype, cld_kind kind, void* stream) {
+    if (!out) return fail(CLD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (nb < 1 || !blk_rows) return fail(CLD_ERR_INVALID, "need nb >= 1 and block row offsets");
+    if (blk_rows[0] != 0) return fail(CLD_ERR_INVALID, "blk_rows[0] must be 0");
+    for (int b = 0; b < nb; ++b)
+        if (blk_rows[b + 1] < blk_rows[b]) return fail(CLD_ERR_INVALID, "blk_rows must not decrease");
+    cld_handle h = nullptr;
+    cld_status st = cld_create_csr(&h, blk_rows[nb], nnz, rowptr, col, val, val_dtype, kind, stream);
+    if (st != CLD_OK) return st;
+    h->nb = nb;
+    h->blk_rows.assign(blk_rows, blk_rows + nb + 1);
+    h->max_tiles = 0;
+    for (int b = 0; b < nb; ++b) h->max_tiles += (blk_rows[b + 1] - blk_rows[b] + 255) / 256;
+    h->impl = 0;  // small blocks: per-lane loads
+    build_tiles(h);
+    *out = h;
+    return CLD_OK;
+}
+
+cld_status cld_batch_set_tile_rows(cld_handle h, int rows) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (h->nb == 0) return fail(CLD_ERR_INVALID, "not a batch handle");
+    if (rows < 256 || rows > (1 << 20)) return fail(CLD_ERR_INVALID, "tile rows must be in [256, 2^20]");
+    h->tile_rows = rows;
+    build_tiles(h);
+    if (h->ws) {
+        const Layout L = make_layout(h, 0, 1, 0);
+        cld_status st = upload_batch_tables(h, L);
+        if (st != CLD_OK) return st;
+    }
+    return CLD_OK;
+}
+
+cld_status cld_batch_set_intervals(cld_handle h, const double* a, const double* b) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (h->nb == 0) return fail(CLD_ERR_INVALID, "not a batch handle");
+    if (!a || !b) return fail(CLD_ERR_INVALID, "NULL interval arrays");
+    for (int k = 0; k < h->nb; ++k)
+        if (!(a[k] > 0.0) || !(a[k] < b[k]) || !isfinite(a[k]) || !isfinite(b[k]))
+            return fail(CLD_ERR_INTERVAL, "block %d: interval must satisfy 0 < a < b (got [%g, %g])", k, a[k], b[k]);
+    h->ba.assign(a, a + h->nb);
+    h->bb.assign(b, b + h->nb);
+    h->have_bintervals = true;
+    if (h->ws) return apply_bintervals(h, make_layout(h, 0, 1, 0));
+    return CLD_OK;
+}
+
+cld_status cld_batch_auto_intervals(cld_handle h, double* a_out, double* b_out) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (h->nb == 0) return fail(CLD_ERR_INVALID, "not a batch handle");
+    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
+    const Layout L = make_layout(h, 0, 1, 0);
+    BatchAuxArgs x = batch_aux_args(h, L);
+    CUDA_TRY(cudaMemsetAsync(x.flags, 0, 4, h->stream));
+    CUDA_TRY(launch_batch_aux(h->kind == CLD_GENERAL ? 5 : 4, h->nb, 1, h->stream, x));
+    std::vector<Params> p((size_t)h->nb);
+    CUDA_TRY(cudaMemcpyAsync(p.data(), x.bprm, sizeof(Params) * h->nb, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->ba.resize(h->nb);
+    h->bb.resize(h->nb);
+    int bad = -1;
+    for (int k = 0; k < h->nb; ++k) {
+        h->ba[k] = p[k].a;
+        h->bb[k] = p[k].b;
+        if (a_out) a_out[k] = p[k].a;
+        if (b_out) b_out[k] = p[k].b;
+        if (!p[k].interval_ok && bad < 0) bad = k;
+    }
+    if (bad >= 0) {
+        h->have_bintervals = false;
+        return fail(CLD_ERR_INTERVAL, "block %d: computed interval [%g, %g] is not a valid 0 < a < b", bad,
+                    p[bad].a, p[bad].b);
+    }
+    h->have_bintervals = true;
+    return CLD_OK;
+}
+
+cld_status cld_batch_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out, double* stderr_out) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (h->nb == 0) return fail(CLD_ERR_INVALID, "not a batch handle");
+    if (n < 0 || M < 1 || n > 100000) return fail(CLD_ERR_INVALID, "need 0 <= n <= 100000 and M >= 1");
+    if (!logdet_out) return fail(CLD_ERR_INVALID, "logdet_out is NULL");
+    if (!h->have_bintervals) return fail(CLD_ERR_INTERVAL, "no block intervals set");
+    if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
+    const Layout L = make_layout(h, n, M, 0);
+    if (h->ws_bytes < L.total)
+        return fail(CLD_ERR_NOMEM, "workspace has %zu bytes, %zu needed", h->ws_bytes, L.total);
+    cld_status st;
+    if (h->use_graph) {
+        BatchAuxArgs x = batch_aux_args(h, L);
+        x.seed = seed;
+        CUDA_TRY(launch_batch_aux(0, h->nb, 1, h->stream, x));
+        st = run_graph(h, 2, n, M, [&]() { return enqueue_batch(h, L, n, M, seed, false); });
+        ++h->last_total_launches;
+    } else {
+        st = enqueue_batch(h, L, n, M, seed, true);
+    }
+    if (st != CLD_OK) return st;
+    std::vector<Result> r((size_t)h->nb);
+    CUDA_TRY(cudaMemcpyAsync(r.data(), at<Result>(h, L.bres), sizeof(Result) * h->nb, cudaMemcpyDeviceToHost,
+                             h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    int bad = -1;
+    for (int k = 0; k < h->nb; ++k) {
+        logdet_out[k] = r[k].logdet;
+        if (stderr_out) stderr_out[k] = r[k].stderr_;
+        if (r[k].spectrum_bad && bad < 0) bad = k;
+    }
+    if (bad >= 0)
+        return fail(CLD_ERR_SPECTRUM, "block %d: max |t_jp|/d = %g exceeds 1: spectrum not inside [%g, %g]", bad,
+                    r[bad].max_ratio, h->ba[bad], h->bb[bad]);
+    return CLD_OK;
+}
+
+cld_status cld_set_graph(cld_handle h, int on) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    h->use_graph = on != 0;
+    return CLD_OK;
+}
+
 cld_status cld_set_kernel_variant(cld_handle h, int variant) {
     if (check_handle(h)) return CLD_ERR_INVALID;
     if (variant < 0 || variant >= kNumStepImpls)
@@ -613,7 +976,8 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     if (check_handle(h)) return CLD_ERR_INVALID;
     if (M < 1 || reps < 1 || reps > 1000) return fail(CLD_ERR_INVALID, "need M >= 1 and 1 <= reps <= 1000");
     if (!h->ready) return fail(CLD_ERR_NOMEM, "workspace not set");
-    if (!h->have_interval) return fail(CLD_ERR_INTERVAL, "no spectral interval set");
+    if (!(h->nb > 0 ? h->have_bintervals : h->have_interval))
+        return fail(CLD_ERR_INTERVAL, "no spectral interval set");
     if (h->d == 0) return fail(CLD_ERR_INVALID, "empty matrix");
     const int saved = h->impl;
     int best = -1;
@@ -643,10 +1007,23 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
         a.out = at<float>(h, L.W[2]);
         a.tpart = at<double>(h, L.tpart);
         CUDA_TRY(cudaMemsetAsync(at<float>(h, L.W[0]), 0, 3 * ((size_t)h->d * L.panel * 4), h->stream));
-        CUDA_TRY(launch_step(L.panel, (int)h->dtype, kStepGeneral, L.grid, h->stream, a));  // warm-up
+        BatchStepArgs ba{};
+        int bgrid = L.grid;
+        if (h->nb > 0) {  // batches: time the tile-queue kernel
+            ba.s = a;
+            ba.tiles = at<Tile>(h, L.tiles);
+            ba.ntiles = (int64_t)h->tiles.size();
+            ba.bprm = at<Params>(h, L.bprm);
+            ba.tpart = at<double>(h, L.tpart);
+            bgrid = (int)(ba.ntiles < L.grid ? (ba.ntiles > 0 ? ba.ntiles : 1) : L.grid);
+        }
+        auto one = [&]() {
+            return h->nb > 0 ? launch_batch_step(L.panel, (int)h->dtype, kStepGeneral, bgrid, h->stream, ba)
+                             : launch_step(L.panel, (int)h->dtype, kStepGeneral, L.grid, h->stream, a);
+        };
+        CUDA_TRY(one());  // warm-up
         CUDA_TRY(cudaEventRecord(e0, h->stream));
-        for (int r = 0; r < reps; ++r)
-            CUDA_TRY(launch_step(L.panel, (int)h->dtype, kStepGeneral, L.grid, h->stream, a));
+        for (int r = 0; r < reps; ++r) CUDA_TRY(one());
         CUDA_TRY(cudaEventRecord(e1, h->stream));
         CUDA_TRY(cudaEventSynchronize(e1));
         float ms = 0.f;

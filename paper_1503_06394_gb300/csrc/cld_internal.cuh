@@ -158,6 +158,55 @@ cudaError_t launch_gershgorin(int64_t d, const int64_t* rowptr, const int32_t* c
 cudaError_t launch_set_params(Params* prm, double a, double b, cudaStream_t s);
 cudaError_t launch_coeffs(int n, const Params* prm, double* coeffs, double* coef_scratch, cudaStream_t s);
 
+// ------------------------------------------------------------------ batches (batch.cu)
+// A row tile of one block of a batch: rows [lo, hi) of block blk.
+struct Tile {
+    int64_t lo, hi;
+    int32_t blk;
+    int32_t pad;
+};
+
+struct BatchStepArgs {
+    StepArgs s;              // matrix, vectors, signs, panel (s.prm unused)
+    const Tile* tiles;
+    int64_t ntiles;
+    const Params* bprm;      // per block
+    double* tpart;           // [ntiles][panel] for this step
+};
+
+struct BatchAuxArgs {
+    Params* bprm;
+    const double* ab;        // interval pairs
+    uint64_t seed;
+    const Tile* tiles;
+    int64_t ntiles;
+    const int64_t* tile_start;
+    const int64_t* blk_rows;
+    int nw;
+    uint32_t panel;          // panel index (probe bits)
+    uint32_t* vbits;
+    const double* tpart;
+    int panel_width, mreal, n, M, pbase, nsteps;
+    double* T;
+    int dtype;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const void* val;
+    const int64_t* rowptrT;
+    const int32_t* colT;
+    const void* valT;
+    uint32_t* flags;
+};
+
+cudaError_t launch_batch_step(int panel, int dtype, StepKind kind, int grid, cudaStream_t s,
+                              const BatchStepArgs& a);
+// what: 0 set seeds, 1 set intervals, 2 probe bits, 3 reduce moments,
+//       4 Gershgorin per block, 5 general bounds per block, 6 block check
+cudaError_t launch_batch_aux(int what, int nb, int grid, cudaStream_t s, const BatchAuxArgs& a);
+cudaError_t launch_finalize_batch(int nb, int n, int M, const int64_t* blk_rows, int general, const Params* prm,
+                                  double* T, double* coeffs, double* coef_scratch, double* gamma_p, Result* res,
+                                  cudaStream_t s);
+
 // ------------------------------------------------------------------ adjoint (adjoint.cu)
 // Arguments of one adjoint pass (see adjoint.cu).
 struct AdjArgs {

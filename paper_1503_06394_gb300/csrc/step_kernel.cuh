@@ -140,6 +140,27 @@ __device__ __forceinline__ float4 row_product(int64_t k0, int64_t k1, const int3
 
 // GATHER: 0 float rows of args.x, 1 probe signs.  PREV: 0 none, 1 v, 2 args.wprev.
 // EPI: 0 plain product, 1 recurrence + moments.  IMPL: inner loop (row_product).
+// The recurrence update of one row's four probes:
+//   y = scale * (X w_j) - shift * w_j        (= At w_j; hi/lo constant pairs,
+//                                             large terms first)
+//   PREV 0: w_1 = y;  otherwise w_{j+1} = 2 y - w_{j-1}  (pv = w_{j-1}).
+template <int PREV>
+__device__ __forceinline__ float4 recurrence_update(float4 acc, float4 own, float4 pv, float scale,
+                                                    float scale_lo, float shift, float shift_lo) {
+    float4 y;
+    y.x = fmaf(scale, acc.x, -shift * own.x) + fmaf(scale_lo, acc.x, -shift_lo * own.x);
+    y.y = fmaf(scale, acc.y, -shift * own.y) + fmaf(scale_lo, acc.y, -shift_lo * own.y);
+    y.z = fmaf(scale, acc.z, -shift * own.z) + fmaf(scale_lo, acc.z, -shift_lo * own.z);
+    y.w = fmaf(scale, acc.w, -shift * own.w) + fmaf(scale_lo, acc.w, -shift_lo * own.w);
+    if (PREV == 0) return y;
+    float4 r;
+    r.x = fmaf(2.f, y.x, -pv.x);
+    r.y = fmaf(2.f, y.y, -pv.y);
+    r.z = fmaf(2.f, y.z, -pv.z);
+    r.w = fmaf(2.f, y.w, -pv.w);
+    return r;
+}
+
 // Resident-CTA targets per variant (256 threads): 6 (40 registers), 3, 4.
 template <int IMPL>
 struct StepOccupancy { static constexpr int value = IMPL == 0 ? 6 : IMPL == 1 ? 3 : 4; };
@@ -212,22 +233,8 @@ __global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_ker
         } else {
             const float4 v = signs4(__ldg(vbits + row * NW + wsel), bsh, mask);
             const float4 own = (PREV == 0) ? v : ldg4(args.own + row * MP + p0);
-            // y = scale * acc - shift * own with the hi/lo constant pairs: the
-            // large terms first, then the small corrections.
-            float4 y;
-            y.x = fmaf(scale, acc.x, -shift * own.x) + fmaf(scale_lo, acc.x, -shift_lo * own.x);
-            y.y = fmaf(scale, acc.y, -shift * own.y) + fmaf(scale_lo, acc.y, -shift_lo * own.y);
-            y.z = fmaf(scale, acc.z, -shift * own.z) + fmaf(scale_lo, acc.z, -shift_lo * own.z);
-            y.w = fmaf(scale, acc.w, -shift * own.w) + fmaf(scale_lo, acc.w, -shift_lo * own.w);
-            if (PREV == 0) {
-                res = y;
-            } else {
-                const float4 pv = (PREV == 1) ? v : ldcs4(args.wprev + row * MP + p0);
-                res.x = fmaf(2.f, y.x, -pv.x);
-                res.y = fmaf(2.f, y.y, -pv.y);
-                res.z = fmaf(2.f, y.z, -pv.z);
-                res.w = fmaf(2.f, y.w, -pv.w);
-            }
+            const float4 pv = (PREV == 2) ? ldcs4(args.wprev + row * MP + p0) : v;
+            res = recurrence_update<PREV>(acc, own, pv, scale, scale_lo, shift, shift_lo);
             tacc.x = fmaf(v.x, res.x, tacc.x);
             tacc.y = fmaf(v.y, res.y, tacc.y);
             tacc.z = fmaf(v.z, res.z, tacc.z);

@@ -1,0 +1,166 @@
+"""Batched estimates (many matrices of uneven size in one pass per step):
+each block against the single-matrix path with seed + b and against the
+oracle; intervals per block; CUDA-graph replay; tile sizes; variants."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from gpu_common import moment_tol, require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_gpu()
+
+
+def spd_mats(sizes, seed):
+    return [workloads.sparse_random_spd(int(d), 3, seed + i) for i, d in enumerate(sizes)]
+
+
+def intervals(mats, general=False):
+    a, b = [], []
+    for m in mats:
+        _, v64 = m.stored("f32")
+        if general:
+            al, be = oracle.dominance_margins(m.rowptr, m.col, v64)
+            lo, hi = al * be, oracle.sigma_max_bound(m.rowptr, m.col, v64) ** 2
+        else:
+            lo, hi = oracle.gershgorin(m.rowptr, m.col, v64)
+        if not hi - lo > 1e-9 * hi:
+            lo, hi = 0.5 * lo, 1.5 * hi
+        a.append(lo)
+        b.append(hi)
+    return np.array(a), np.array(b)
+
+
+SIZES = [1, 2, 31, 32, 33, 300, 1024, 1025, 4000, 7, 2047, 5000, 13, 600]
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2])
+def test_batch_spd_matches_single_and_oracle(torch, variant):
+    from paper_1503_06394_gb300 import CsrBatchLogdet, CsrLogdet
+
+    mats = spd_mats(SIZES, 40)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    a, b = intervals(mats)
+    n, M, seed = 20, 16, 9
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    bt.set_kernel_variant(variant)
+    bt.set_intervals(a, b)
+    r = bt.estimate(n, M, seed)
+    bt.close()
+    for k, m in enumerate(mats):
+        v32, v64 = m.stored("f32")
+        one = CsrLogdet(m.rowptr, m.col, v32)
+        one.set_interval(a[k], b[k])
+        g1 = one.estimate(n, M, seed + k)["logdet"]
+        one.close()
+        ref = oracle.estimate(m.rowptr, m.col, v64, a[k], b[k], n, M, seed=seed + k)
+        # same probes; only the FP32 per-thread moment sums see another row order
+        assert abs(r["logdet"][k] - g1) <= 1e-6 * abs(g1) + 1e-9, (k, r["logdet"][k], g1)
+        assert abs(r["logdet"][k] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"]) + 1e-9
+        if M > 1 and m.d > 1:
+            assert abs(r["stderr"][k] - ref["stderr"]) <= 1e-3 * ref["stderr"] + 1e-9
+
+
+def test_batch_general_matches_oracle(torch):
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = [workloads.nonsymmetric_dominant(int(d), 3, 70 + i) for i, d in enumerate([3, 64, 500, 2500, 1200, 90])]
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32, kind="general")
+    a, b = bt.auto_intervals()
+    ea, eb = intervals(mats, general=True)
+    np.testing.assert_allclose(a, ea, rtol=1e-9)
+    np.testing.assert_allclose(b, eb, rtol=1e-9)
+    n, M = 30, 8
+    r = bt.estimate(n, M, 5)
+    bt.close()
+    for k, m in enumerate(mats):
+        _, v64 = m.stored("f32")
+        ref = oracle.estimate(m.rowptr, m.col, v64, a[k], b[k], n, M, seed=5 + k, kind=1)
+        assert abs(r["logdet"][k] - ref["gamma"] / 2) <= 1e-5 * abs(ref["gamma"] / 2), k
+
+
+def test_batch_auto_intervals_match_oracle(torch):
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = spd_mats([10, 700, 3000, 40], 3)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    a, b = bt.auto_intervals()
+    ea, eb = intervals(mats)
+    np.testing.assert_allclose(a, ea, rtol=1e-12)
+    np.testing.assert_allclose(b, eb, rtol=1e-12)
+    bt.close()
+
+
+def test_graph_replay_is_identical(torch):
+    from paper_1503_06394_gb300 import CsrBatchLogdet, CsrLogdet
+
+    mats = spd_mats([500, 2000, 64], 8)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    a, b = intervals(mats)
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    bt.set_intervals(a, b)
+    plain = [bt.estimate(15, 16, s)["logdet"] for s in (0, 1)]
+    bt.set_graph(True)
+    graph = [bt.estimate(15, 16, s)["logdet"] for s in (0, 1, 0)]
+    bt.close()
+    np.testing.assert_array_equal(plain[0], graph[0])
+    np.testing.assert_array_equal(plain[1], graph[1])
+    np.testing.assert_array_equal(plain[0], graph[2])
+    m = mats[1]
+    v32, _ = m.stored("f32")
+    one = CsrLogdet(m.rowptr, m.col, v32)
+    one.set_interval(a[1], b[1])
+    p = one.estimate(30, 32, 4, moments=True)
+    one.set_graph(True)
+    g = one.estimate(30, 32, 4, moments=True)
+    g2 = one.estimate(30, 32, 5, moments=True)
+    one.set_graph(False)
+    p2 = one.estimate(30, 32, 5, moments=True)
+    one.close()
+    assert p["logdet"] == g["logdet"] and np.array_equal(p["t"], g["t"])
+    assert p2["logdet"] == g2["logdet"]
+
+
+def test_batch_tile_rows(torch):
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = spd_mats([3000, 900, 5000], 21)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    a, b = intervals(mats)
+    res = []
+    for rows in (256, 1024, 4096):
+        bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+        bt.set_tile_rows(rows)
+        bt.set_intervals(a, b)
+        res.append(bt.estimate(20, 32, 2)["logdet"])
+        bt.close()
+    for r in res[1:]:
+        np.testing.assert_allclose(r, res[0], rtol=1e-6)  # FP32 per-thread sums follow the tiling
+
+
+def test_batch_rejects_off_block_columns(torch):
+    from paper_1503_06394_gb300 import CldError, CsrBatchLogdet
+    from paper_1503_06394_gb300 import _binding as Bd
+
+    mats = spd_mats([100, 100], 1)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    col = S.col.copy()
+    col[5] = 150  # row of block 0 pointing into block 1
+    bt = CsrBatchLogdet(br, S.rowptr, col, s32)
+    with pytest.raises(CldError) as e:
+        bt.reserve(5, 4)
+    assert e.value.status == Bd.CLD_ERR_INVALID
+    bt.close()

@@ -268,12 +268,44 @@ def apex_graph(nv: int, extra_edges: int, seed: int) -> Csr:
     return _coo_to_csr(m, rows, cols, vals, "apex_graph(nv=%d,edges=%d,seed=%d)" % (nv, extra_edges, seed))
 
 
+def batch_mixed(count: int, dmin: float, dmax: float, seed: int, picks: int = 3):
+    """``count`` matrices with d log-uniform in [dmin, dmax]: the first half
+    sparse random SPD (as ``sparse_random_spd``), the second half general
+    non-singular (as ``nonsymmetric_dominant``).  Returns (spd list, general list)."""
+    rng = np.random.default_rng(seed)
+    ds = np.exp(rng.uniform(np.log(dmin), np.log(dmax), size=count)).astype(np.int64)
+    seeds = rng.integers(0, 2**31, size=count)
+    half = count // 2
+    spd = [sparse_random_spd(int(ds[i]), picks, int(seeds[i])) for i in range(half)]
+    gen = [nonsymmetric_dominant(int(ds[i]), picks, int(seeds[i])) for i in range(half, count)]
+    return spd, gen
+
+
+def block_diag(mats):
+    """(blk_rows, Csr) of the block-diagonal matrix with global indices."""
+    ds = np.array([m.d for m in mats], dtype=np.int64)
+    blk_rows = np.zeros(len(mats) + 1, dtype=np.int64)
+    np.cumsum(ds, out=blk_rows[1:])
+    nnzs = np.array([m.nnz for m in mats], dtype=np.int64)
+    noff = np.zeros(len(mats) + 1, dtype=np.int64)
+    np.cumsum(nnzs, out=noff[1:])
+    rowptr = np.zeros(int(blk_rows[-1]) + 1, dtype=np.int64)
+    col = np.empty(int(noff[-1]), dtype=np.int32)
+    val = np.empty(int(noff[-1]), dtype=np.float64)
+    for b, m in enumerate(mats):
+        rowptr[blk_rows[b] + 1:blk_rows[b + 1] + 1] = m.rowptr[1:] + noff[b]
+        col[noff[b]:noff[b + 1]] = m.col + blk_rows[b]
+        val[noff[b]:noff[b + 1]] = m.val
+    return blk_rows, Csr(rowptr, col, val, "block_diag(%d)" % len(mats))
+
+
 # Named workloads of the benchmark and the parity tests.
 CONFIGS = {
     0: dict(kind="sparse_random_spd", d=2048, picks=3, seed=1000, n=30, M=30, probe_seed=0),
     1: dict(kind="grid_gmrf", N=1000, kappa2=0.1, n=50, M=64, probe_seed=0),
     2: dict(kind="sparse_random_spd", d=10_000_000, picks=5, seed=1002, n=100, M=32, probe_seed=0),
     3: dict(kind="wendland", npts=1_000_000, ell=0.002, sigma2=0.1, seed=1003, n=60, M=32, probe_seed=0),
+    4: dict(kind="batch", count=512, dmin=1e3, dmax=2e5, seed=1004, n=40, M=16, probe_seed=0),
 }
 
 
