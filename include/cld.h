@@ -86,6 +86,22 @@ CLD_API cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const
                           const int32_t* col, const void* val, cld_dtype val_dtype,
                           cld_kind kind, void* stream);
 
+/* Creates a handle for a DENSE d x d symmetric positive definite matrix B on
+ * the device (a kernel matrix, say), stored row-major in BF16 with leading
+ * dimension ld (elements; ld >= d, ld a multiple of 8, base 16-byte
+ * aligned).  Each recurrence step is then the product B W_j (d x d by d x P)
+ * on the tensor cores (tcgen05, BF16 inputs, FP32 accumulation, W_j split
+ * into three BF16 parts so the product keeps FP32 accuracy), followed by the
+ * same recurrence epilogue.  The cost per step is one pass over B, O(d^2)
+ * instead of O(nnz) (Sec. 3.1: O(mn ||B||_0)).  cld_workspace_size,
+ * cld_set_workspace, cld_set_interval, cld_auto_interval (Gershgorin, no
+ * Lanczos), cld_estimate and cld_set_graph apply.  Errors: CLD_ERR_INVALID,
+ * CLD_ERR_UNSUPPORTED (dtype other than CLD_BF16, kind other than CLD_SPD);
+ * cld_estimate returns CLD_ERR_TIMEOUT if a pipeline wait on the device gave
+ * up (results invalid). */
+CLD_API cld_status cld_create_dense(cld_handle* out, int64_t d, int64_t ld, const void* val_dev,
+                                    cld_dtype val_dtype, cld_kind kind, void* stream);
+
 /* Bytes of device workspace an estimate of degree n with M probes needs
  * (with_grad != 0: also enough for cld_grad).  Errors: CLD_ERR_INVALID. */
 CLD_API cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes);

@@ -16,7 +16,7 @@ thin Python binding:
 """
 from ._binding import *  # noqa: F401,F403
 from ._binding import CldError, load  # noqa: F401
-from .api import CsrBatchLogdet, CsrLogdet, logdet, logdet_host  # noqa: F401
+from .api import CsrBatchLogdet, CsrLogdet, DenseLogdet, logdet, logdet_host  # noqa: F401
 
 
 def autograd_logdet(values, rowptr, col, n, M, seed=0, interval=(None, None)):

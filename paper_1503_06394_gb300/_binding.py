@@ -28,6 +28,7 @@ _vp, _i64, _i32, _u64, _f64, _sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
 _P = ctypes.POINTER
 SIGNATURES = [
     ("cld_create_csr", _i32, [_P(_vp), _i64, _i64, _vp, _vp, _vp, _i32, _i32, _vp]),
+    ("cld_create_dense", _i32, [_P(_vp), _i64, _i64, _vp, _i32, _i32, _vp]),
     ("cld_workspace_size", _i32, [_vp, _i32, _i32, _i32, _P(_sz)]),
     ("cld_set_workspace", _i32, [_vp, _vp, _sz]),
     ("cld_set_interval", _i32, [_vp, _f64, _f64]),
@@ -112,6 +113,12 @@ def cld_create_csr(d, nnz, rowptr, col, val, val_dtype, kind, stream=0):
     h = ctypes.c_void_p()
     _check(load().cld_create_csr(ctypes.byref(h), d, nnz, _ptr(rowptr), _ptr(col), _ptr(val),
                                  val_dtype, kind, stream or None))
+    return h.value
+
+
+def cld_create_dense(d, ld, val, val_dtype, kind, stream=0):
+    h = ctypes.c_void_p()
+    _check(load().cld_create_dense(ctypes.byref(h), d, ld, _ptr(val), val_dtype, kind, stream or None))
     return h.value
 
 

@@ -130,6 +130,41 @@ class CsrLogdet:
             pass
 
 
+class DenseLogdet(CsrLogdet):
+    """A dense d x d SPD matrix (BF16, row-major, leading dimension ld) on the
+    tensor-core path.  ``matrix``: a torch.bfloat16 CUDA tensor of shape
+    (d, ld) or (d, d), or a numpy uint16 array of BF16 bit patterns."""
+
+    def __init__(self, matrix, d=None, device="cuda", stream=None):
+        torch = _torch()
+        self.torch = torch
+        self.device = torch.device(device)
+        if isinstance(matrix, np.ndarray):
+            if matrix.dtype != np.uint16:
+                raise TypeError("numpy input must be uint16 BF16 bit patterns")
+            t = torch.from_numpy(matrix.view(np.int16)).to(self.device).view(torch.bfloat16)
+        else:
+            if matrix.dtype != torch.bfloat16:
+                raise TypeError("dense matrix must be torch.bfloat16")
+            t = matrix.to(self.device)
+        rows, cols = t.shape
+        self.d = int(d if d is not None else rows)
+        ld = (cols + 7) // 8 * 8
+        if ld != cols or not t.is_contiguous():
+            pad = torch.zeros((rows, ld), dtype=torch.bfloat16, device=self.device)
+            pad[:, :cols] = t
+            t = pad
+        self.val = t
+        self.ld = ld
+        self.nnz = 0
+        self.dtype = "bf16"
+        self.kind = "spd"
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.h = B.cld_create_dense(self.d, ld, self.val, B.CLD_BF16, B.CLD_SPD, self.stream.cuda_stream)
+        self.ws = None
+        self.ws_bytes = 0
+
+
 class CsrBatchLogdet(CsrLogdet):
     """Many matrices in one block-diagonal CSR (global indices); block b holds
     rows [blk_rows[b], blk_rows[b+1]).  estimate() returns per-block arrays."""

@@ -88,6 +88,10 @@ struct cld_ctx {
     std::vector<double> ba, bb;  // per-block intervals
     bool have_bintervals = false;
 
+    // dense matrix (tensor-core path): d x d, leading dimension ld, values in val
+    bool dense = false;
+    int64_t ld = 0;
+
     // CUDA graph of one estimate (set-seed stays outside the graph)
     bool use_graph = false;
     cudaStream_t cap_stream = nullptr;
@@ -108,8 +112,12 @@ struct Layout {
     size_t coeffs, coef_scratch, T, gamma_p, tpart, gpart, vbits, W[3], Y, lanczos, total;
     size_t Wall, lam[3], H;  // gradient: w_1..w_n, the adjoint ring, per-entry sums
     size_t blk_rows, tile_start, tiles, bprm, ab, bres;  // batches
+    size_t xt[2];            // dense: BF16 splits of w_j, [3][panel][dx], double-buffered
+    int64_t dx;
     int panel, nw, grid, ggrid;
 };
+
+static int panel_for_dense(int M) { return M <= 32 ? 32 : M <= 64 ? 64 : 128; }
 
 static int panel_for(int M) {
     if (M >= kMaxPanel) return kMaxPanel;
@@ -156,9 +164,9 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
     L.run = o;
     const int nn = n > 0 ? n : 0;
     const int MM = M > 0 ? M : 1;
-    L.panel = panel_for(MM);
+    L.panel = h->dense ? panel_for_dense(MM) : panel_for(MM);
     L.nw = sign_words(L.panel);
-    L.grid = step_grid(h, L.panel);
+    L.grid = h->dense ? (int)((h->d + 127) / 128) : step_grid(h, L.panel);
     L.ggrid = stream_grid(h);
     L.coeffs = o; o += align_up((size_t)nprob * (nn + 1) * 8);
     L.coef_scratch = o; o += align_up((size_t)nprob * 5 * (nn + 1) * 8);
@@ -172,6 +180,10 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
     const size_t wb = align_up((size_t)h->d * L.panel * 4);
     for (int i = 0; i < 3; ++i) { L.W[i] = o; o += wb; }
     if (h->kind == CLD_GENERAL) { L.Y = o; o += wb; }
+    if (h->dense) {
+        L.dx = (h->d + 63) / 64 * 64;
+        for (int i = 0; i < 2; ++i) { L.xt[i] = o; o += align_up((size_t)3 * L.panel * L.dx * 2); }
+    }
     // Lanczos scratch (5 FP64 vectors + scalars) reuses the W buffers when they are
     // large enough, else gets its own region.
     const size_t lz = align_up((size_t)5 * h->d * 8) + align_up((size_t)(8000 + L.ggrid + 64) * 8);
@@ -255,6 +267,52 @@ static cld_status enqueue_panel_forward(cld_ctx* h, const Layout& L, int n, int 
                                        h->stream));
         ++*launches;
     }
+    return CLD_OK;
+}
+
+// Dense tensor-core path: per panel, the split of the signs, n GEMM steps,
+// the moment reduction; then the final sums.
+static cld_status enqueue_dense(cld_ctx* h, const Layout& L, int n, int M, uint64_t seed, bool with_seed) {
+    Params* prm = at<Params>(h, L.params);
+    uint32_t* vbits = at<uint32_t>(h, L.vbits);
+    double* tpart = at<double>(h, L.tpart);
+    uint32_t* err = at<uint32_t>(h, L.flags) + 1;
+    float* W[3] = {at<float>(h, L.W[0]), at<float>(h, L.W[1]), at<float>(h, L.W[2])};
+    void* xt[2] = {h->ws + L.xt[0], h->ws + L.xt[1]};
+    int launches = 0;
+    if (with_seed) {
+        CUDA_TRY(launch_set_seed(prm, seed, h->stream));
+        ++launches;
+    }
+    const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
+    for (int pk = 0; pk < npanels; ++pk) {
+        const int pbase = pk * kMaxPanel;
+        const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
+        CUDA_TRY(launch_probe_bits(h->d, L.nw, (uint32_t)pk, prm, vbits, L.ggrid, h->stream));
+        CUDA_TRY(launch_dense_sign_split(h->d, L.dx, L.panel, mreal, vbits, xt[0], L.ggrid, h->stream));
+        launches += 2;
+        for (int j = 0; j < n; ++j) {
+            const int prev = j == 0 ? 0 : j == 1 ? 1 : 2;
+            cudaError_t e = launch_dense_step(L.panel, prev, h->d, h->ld, h->val, xt[j % 2], L.dx,
+                                              j >= 1 ? W[j % 3] : nullptr, j >= 2 ? W[(j - 1) % 3] : nullptr,
+                                              W[(j + 1) % 3], xt[(j + 1) % 2], vbits,
+                                              tpart + (size_t)j * L.grid * L.panel, prm, mreal, err, h->stream);
+            if (e == cudaErrorNotSupported) return fail(CLD_ERR_UNSUPPORTED, "TMA tensor map encoding unavailable");
+            if (e != cudaSuccess) return fail(CLD_ERR_CUDA, "dense step launch: %s", cudaGetErrorString(e));
+            ++launches;
+        }
+        if (n > 0) {
+            CUDA_TRY(launch_reduce_moments(tpart, n, L.grid, L.panel, mreal, M, pbase, at<double>(h, L.T),
+                                           h->stream));
+            ++launches;
+        }
+    }
+    CUDA_TRY(launch_finalize(n, M, h->d, 0, prm, at<double>(h, L.T), at<double>(h, L.coeffs),
+                             at<double>(h, L.coef_scratch), at<double>(h, L.gamma_p), at<Result>(h, L.result),
+                             h->stream));
+    ++launches;
+    h->last_total_launches = launches;
+    h->last_step_launches = 0;
     return CLD_OK;
 }
 
@@ -564,7 +622,7 @@ cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes) {
     h->ready = false;
     uint32_t* flags = at<uint32_t>(h, L.flags);
     CUDA_TRY(cudaMemsetAsync(flags, 0, 256, h->stream));
-    if (h->d > 0)
+    if (h->d > 0 && !h->dense)
         CUDA_TRY(launch_validate_csr(h->d, h->nnz, h->rowptr, h->col, h->val, (int)h->dtype, flags,
                                      stream_grid(h), h->stream));
     uint32_t f = 0;
@@ -624,7 +682,11 @@ cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a_out, dou
     Params* prm = at<Params>(h, L.params);
     uint32_t* flags = at<uint32_t>(h, L.flags);
     CUDA_TRY(cudaMemsetAsync(flags, 0, 4, h->stream));
-    if (h->kind == CLD_SPD) {
+    if (h->dense) {
+        if (lanczos_iters > 0) return fail(CLD_ERR_UNSUPPORTED, "Lanczos is available for CSR matrices");
+        CUDA_TRY(launch_dense_gershgorin(h->d, h->ld, h->val, at<double>(h, L.gpart), L.ggrid, prm, flags,
+                                         h->stream));
+    } else if (h->kind == CLD_SPD) {
         CUDA_TRY(launch_gershgorin(h->d, h->rowptr, h->col, h->val, (int)h->dtype, at<double>(h, L.gpart),
                                    L.ggrid, prm, flags, h->stream));
         if (lanczos_iters > 0)
@@ -674,17 +736,25 @@ cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logde
         return CLD_OK;
     }
     cld_status st;
+    uint32_t* err = at<uint32_t>(h, L.flags) + 1;
+    if (h->dense) CUDA_TRY(cudaMemsetAsync(err, 0, 4, h->stream));
+    auto body = [&](bool with_seed) {
+        return h->dense ? enqueue_dense(h, L, n, M, seed, with_seed) : enqueue_estimate(h, L, n, M, seed, with_seed);
+    };
     if (h->use_graph) {
         CUDA_TRY(launch_set_seed(at<Params>(h, L.params), seed, h->stream));
-        st = run_graph(h, 1, n, M, [&]() { return enqueue_estimate(h, L, n, M, seed, false); });
+        st = run_graph(h, h->dense ? 3 : 1, n, M, [&]() { return body(false); });
         ++h->last_total_launches;
     } else {
-        st = enqueue_estimate(h, L, n, M, seed, true);
+        st = body(true);
     }
     if (st != CLD_OK) return st;
+    uint32_t derr = 0;
+    if (h->dense) CUDA_TRY(cudaMemcpyAsync(&derr, err, 4, cudaMemcpyDeviceToHost, h->stream));
     Result r{};
     st = read_result(h, L, n, M, logdet_out, stderr_out, moments_out, &r);
     if (st != CLD_OK) return st;
+    if (derr) return fail(CLD_ERR_TIMEOUT, "a dense-step pipeline wait gave up (results invalid)");
     if (r.spectrum_bad)
         return fail(CLD_ERR_SPECTRUM,
                     "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]", r.max_ratio,
@@ -708,8 +778,8 @@ cld_status cld_last_details(cld_handle h, double* coeffs_out, double* gamma_p_ou
 
 cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out, float* dvalues_dev) {
     if (check_handle(h)) return CLD_ERR_INVALID;
-    if (h->kind != CLD_SPD || h->nb > 0)
-        return fail(CLD_ERR_UNSUPPORTED, "cld_grad supports single CLD_SPD matrices only");
+    if (h->kind != CLD_SPD || h->nb > 0 || h->dense)
+        return fail(CLD_ERR_UNSUPPORTED, "cld_grad supports single sparse CLD_SPD matrices only");
     if (n < 0 || M < 1 || n > 100000) return fail(CLD_ERR_INVALID, "need 0 <= n <= 100000 and M >= 1");
     if (!logdet_out) return fail(CLD_ERR_INVALID, "logdet_out is NULL");
     if (!dvalues_dev && h->nnz > 0) return fail(CLD_ERR_INVALID, "dvalues_dev is NULL");
@@ -841,6 +911,36 @@ cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* rowptr_hos
     return st;
 }
 
+
+cld_status cld_create_dense(cld_handle* out, int64_t d, int64_t ld, const void* val_dev, cld_dtype val_dtype,
+                            cld_kind kind, void* stream) {
+    if (!out) return fail(CLD_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (d < 1 || ld < d) return fail(CLD_ERR_INVALID, "need d >= 1 and ld >= d");
+    if (!val_dev) return fail(CLD_ERR_INVALID, "NULL matrix");
+    if (val_dtype != CLD_BF16)
+        return fail(CLD_ERR_UNSUPPORTED, "the dense tensor-core path takes BF16 values");
+    if (kind != CLD_SPD) return fail(CLD_ERR_UNSUPPORTED, "the dense path takes symmetric positive definite B");
+    if (ld % 8 != 0 || ((uintptr_t)val_dev) % 16 != 0)
+        return fail(CLD_ERR_INVALID, "dense rows must start 16-byte aligned (ld multiple of 8, aligned base)");
+    cld_ctx* h = new (std::nothrow) cld_ctx;
+    if (!h) return fail(CLD_ERR_NOMEM, "host allocation failed");
+    h->d = d;
+    h->nnz = 0;
+    h->val = val_dev;
+    h->dtype = val_dtype;
+    h->kind = kind;
+    h->stream = (cudaStream_t)stream;
+    h->dense = true;
+    h->ld = ld;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return fail(CLD_ERR_CUDA, "no CUDA device");
+    }
+    *out = h;
+    return CLD_OK;
+}
 
 cld_status cld_create_batch(cld_handle* out, int nb, const int64_t* blk_rows, int64_t nnz, const int64_t* rowptr,
                             const int32_t* col, const void* val, cld_dtype val_dtype, cld_kind kind, void* stream) {
@@ -979,6 +1079,7 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     if (!(h->nb > 0 ? h->have_bintervals : h->have_interval))
         return fail(CLD_ERR_INTERVAL, "no spectral interval set");
     if (h->d == 0) return fail(CLD_ERR_INVALID, "empty matrix");
+    if (h->dense) return fail(CLD_ERR_UNSUPPORTED, "the dense path has a single kernel");
     const int saved = h->impl;
     int best = -1;
     float best_ms = 0.f;
