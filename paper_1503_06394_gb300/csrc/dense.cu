@@ -152,7 +152,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // ------------------------------------------------------------------ the step
 template <int P>
 struct DenseSmem {
-    static constexpr int kStages = P <= 64 ? 4 : 2;   // ring depth (fits 227 KB)
+    // ring depth: 3 at P = 32 leaves room for two CTAs per SM (104 KB each),
+    // so one CTA's epilogue overlaps another's main loop; 4 at P = 64; 2 at 128
+    static constexpr int kStages = P == 32 ? 3 : P == 64 ? 4 : 2;
     static constexpr int kA = kDRows * kDK * 2;        // 16 KB
     static constexpr int kX = kDSplit * P * kDK * 2;   // 3 parts x P rows x 128 B
     static constexpr int kStage = kA + kX;
@@ -162,7 +164,7 @@ struct DenseSmem {
 };
 
 template <int P, int PREV>
-__global__ void __launch_bounds__(kDThreads, 1)
+__global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
     dense_step_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                       const DenseArgs args) {
     using S = DenseSmem<P>;
@@ -171,7 +173,7 @@ __global__ void __launch_bounds__(kDThreads, 1)
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned ring (swizzle atoms)
     uint8_t* gbase = smem_raw + (base - raw);
-    const uint32_t bars = base + S::kStage * kDStages;  // full[4], empty[4], accum
+    const uint32_t bars = base + S::kStage * kDStages;  // full[S], empty[S], accum
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S::kStage * kDStages + 9 * 8);
     int* fail = reinterpret_cast<int*>(gbase + S::kStage * kDStages + 9 * 8 + 4);
     float* tr = reinterpret_cast<float*>(gbase + S::kStage * kDStages + 256);  // [128][P+1]
