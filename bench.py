@@ -226,6 +226,18 @@ def time_estimates(m, n, M, seed, interval, steps, warmup, torch, world):
     return total_ms / steps, step_ms / max(1, step_launches), step_launches, total_launches, r
 
 
+def run_only(args):
+    """One leg alone (profiling captures on smaller cases): prints its JSON."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    leg = {"dense": dense_leg, "adjoint": adjoint_leg}[args.only]
+    out = leg(args, torch) if args.only == "dense" else leg(args, torch, 1)
+    print(json.dumps({"only": args.only, **out}), flush=True)
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -290,6 +302,9 @@ def run_ours(args, rank, world):
     batched = None
     if not args.no_batch and args.d is None:
         batched = batch_leg(args, torch)
+    dense = None
+    if not args.no_dense and args.d is None:
+        dense = dense_leg(args, torch)
 
     # end to end through the host-buffer entry point (pinned host arrays)
     rp = torch.from_numpy(B.rowptr).pin_memory()
@@ -340,6 +355,8 @@ def run_ours(args, rank, world):
         line["adjoint"] = adjoint
     if batched is not None:
         line["batched"] = batched
+    if dense is not None:
+        line["dense"] = dense
     if not args.no_cpu_baseline:
         # the oracle on the original FP64 values, probe 0: the CPU baseline and
         # the reference for the relative errors of the FP32 and BF16 results
@@ -365,7 +382,12 @@ def adjoint_leg(args, torch, world):
     every w_j + reverse pass + gradient map) on the same matrix and probes."""
     from paper_1503_06394_gb300 import CsrLogdet
 
-    cfg = workloads.CONFIGS[3]
+    cfg = dict(workloads.CONFIGS[3])
+    if args.d:
+        cfg["npts"] = int(args.d)
+        cfg["ell"] = 0.002 * (1e6 / args.d) ** 0.5  # same expected neighbour count
+    if args.n:
+        cfg["n"] = int(args.n)
     K = workloads.make(cfg)
     v32, _ = K.stored("f32")
     n, M = cfg["n"], cfg["M"]
@@ -485,6 +507,43 @@ def batch_leg(args, torch):
     return out
 
 
+def dense_leg(args, torch):
+    """Dense kernel-matrix path (tensor cores): a d = 32768 BF16 SPD matrix
+    (2.1 GB), n = 30, M = 32.  The step streams B once: bytes per step =
+    2 d^2 + 12 d M (vectors); the MMA work is 3 x 2 d^2 M (three BF16 parts)."""
+    from paper_1503_06394_gb300 import DenseLogdet
+
+    d, n, M = args.d or 32768, args.n or 30, 32
+    g = torch.Generator(device="cuda").manual_seed(1005)
+    A = (torch.rand((d, d), device="cuda", generator=g) * 2 - 1) * (0.5 / d)
+    A = (A + A.T) / 2
+    A.fill_diagonal_(1.0)
+    Ab = A.to(torch.bfloat16)
+    del A
+    m = DenseLogdet(Ab, d)
+    a, b = m.auto_interval(0)
+    m.estimate(n, M, 0)
+    steps = max(1, args.steps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        r = m.estimate(n, M, 0)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    m.close()
+    del m, Ab
+    torch.cuda.empty_cache()
+    peak, src = read_peaks()
+    step_bytes = 2 * d * d + 12 * d * M
+    gbs = n * step_bytes / (ms / 1e3) / 1e9
+    return {"workload": "dense SPD, BF16, d=%d (uniform off-diagonals, unit diagonal), n=%d, M=%d" % (d, n, M),
+            "interval": [a, b], "ms_per_estimate": ms, "gbs": gbs, "pct_of_peak": 100 * gbs / peak,
+            "tensor_tflops": n * 3 * 2 * d * d * M / (ms / 1e3) / 1e12, "logdet": r["logdet"],
+            "kernel": "dense_step_kernel (tcgen05.mma kind::f16, TMA, TMEM)"}
+
+
 def profiled_traffic(args, B):
     """DRAM bytes (read + write) per general-step launch from the committed ncu
     summary of this workload, if the step kernel's source is unchanged since."""
@@ -519,6 +578,10 @@ def main():
     ap.add_argument("--no-bf16", action="store_true", help="skip the BF16-storage measurement")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward (config 3) measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) measurement")
+    ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core measurement")
+    ap.add_argument("--only", choices=["dense", "adjoint"], default=None,
+                    help="run one leg alone (with --d / --n overrides) and print its JSON")
+    ap.add_argument("--n", type=int, default=None, help="degree override for --only")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -531,6 +594,8 @@ def main():
         torch.distributed.init_process_group(backend)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.only:
+        run_only(args)
     else:
         run_ours(args, rank, world)
     if world > 1:
