@@ -233,8 +233,8 @@ def run_only(args):
     import __graft_entry__
 
     __graft_entry__.build()
-    leg = {"dense": dense_leg, "adjoint": adjoint_leg}[args.only]
-    out = leg(args, torch) if args.only == "dense" else leg(args, torch, 1)
+    leg = {"dense": dense_leg, "adjoint": adjoint_leg, "paper": paper_leg, "latency": latency_leg}[args.only]
+    out = leg(args, torch, 1) if args.only == "adjoint" else leg(args, torch)
     print(json.dumps({"only": args.only, **out}), flush=True)
 
 
@@ -305,6 +305,9 @@ def run_ours(args, rank, world):
     dense = None
     if not args.no_dense and args.d is None:
         dense = dense_leg(args, torch)
+    latency = None
+    if not args.no_latency and args.d is None:
+        latency = latency_leg(args, torch)
 
     # end to end through the host-buffer entry point (pinned host arrays)
     rp = torch.from_numpy(B.rowptr).pin_memory()
@@ -357,6 +360,8 @@ def run_ours(args, rank, world):
         line["batched"] = batched
     if dense is not None:
         line["dense"] = dense
+    if latency is not None:
+        line["latency"] = latency
     if not args.no_cpu_baseline:
         # the oracle on the original FP64 values, probe 0: the CPU baseline and
         # the reference for the relative errors of the FP32 and BF16 results
@@ -507,6 +512,84 @@ def batch_leg(args, torch):
     return out
 
 
+def paper_leg(args, torch):
+    """The paper's timing experiment (Sec. 5.1, Fig. 1a): Algorithm 2 on its own
+    sparse random generator (five U[-1,1] off-diagonals per row, mirrored,
+    diagonal = absolute row sum + 1e-3) with m = 10, n = 15,
+    sigma_min = 1e-3, sigma_max = ||C||_1, at d = 3e7 (about 3e8 stored
+    entries).  The paper reports 500 s on a 3.40 GHz Intel i7.  Accuracy point:
+    the same setting at d = 1e4 against numpy's log|det C|."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    n, M = 15, 10
+    out = {"paper_seconds": 500.0, "paper_hardware": "3.40 GHz Intel i7, 24 GB RAM (Sec. 5.1)"}
+    for d in (10_000, args.d or 30_000_000):
+        t0 = time.time()
+        C = workloads.paper_sparse_random(d, 1006)
+        gen = time.time() - t0
+        v32, v64 = C.stored("f32")
+        smax = float(np.max(np.add.reduceat(np.abs(v64), C.rowptr[:-1])))  # ||C||_1 = ||C||_inf (symmetric)
+        m = CsrLogdet(C.rowptr, C.col, v32, kind="general")
+        m.set_interval(1e-6, smax ** 2)
+        m.reserve(n, M)
+        m.estimate(n, M, 0)
+        torch.cuda.synchronize()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = m.estimate(n, M, 0)
+        torch.cuda.synchronize()
+        sec = (time.perf_counter() - t0) / reps
+        m.close()
+        key = "d%d" % d
+        out[key] = {"nnz": C.nnz, "seconds": sec, "logdet": r["logdet"], "stderr": r["stderr"],
+                    "speedup_vs_paper": (500.0 / sec) if d >= 30_000_000 else None, "generation_s": gen}
+        if d <= 20000:
+            exact = float(np.linalg.slogdet(C.dense())[1])
+            out[key]["exact"] = exact
+            out[key]["rel_err"] = abs(r["logdet"] - exact) / abs(exact)
+        del C, v32, v64
+        torch.cuda.empty_cache()
+    return out
+
+
+def latency_leg(args, torch):
+    """Config 0 (d = 2048, n = 30, M = 30): a launch- and latency-bound size.
+    Time per estimate with plain launches and with the whole estimate replayed
+    as one CUDA graph; errors against the oracle (same probes) and against the
+    exact Cholesky value."""
+    import oracle
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    cfg = workloads.CONFIGS[0]
+    B = workloads.make(cfg)
+    v32, v64 = B.stored("f32")
+    n, M = cfg["n"], cfg["M"]
+    a, b = oracle.gershgorin(B.rowptr, B.col, v64)
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    m.set_interval(a, b)
+    m.reserve(n, M)
+    out = {"workload": "sparse_random_spd d=%d picks=%d seed=%d, n=%d, M=%d" % (B.d, cfg["picks"], cfg["seed"], n, M)}
+    reps = 50
+    for mode in ("launches", "graph"):
+        m.set_graph(mode == "graph")
+        for _ in range(5):
+            r = m.estimate(n, M, cfg["probe_seed"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = m.estimate(n, M, cfg["probe_seed"])
+        out["%s_us" % mode] = (time.perf_counter() - t0) / reps * 1e6
+    m.close()
+    ref = oracle.estimate(B.rowptr, B.col, v64, a, b, n, M, seed=cfg["probe_seed"])
+    exact = oracle.logdet_cholesky(workloads.Csr(B.rowptr, B.col, v64).dense())
+    out.update({"logdet": r["logdet"], "stderr": r["stderr"], "exact_cholesky": exact,
+                "rel_err_vs_oracle": abs(r["logdet"] - ref["gamma"]) / abs(ref["gamma"]),
+                "rel_err_vs_exact": abs(r["logdet"] - exact) / abs(exact),
+                "timing": "host wall clock per estimate call (includes the result read-back)"})
+    return out
+
+
 def dense_leg(args, torch):
     """Dense kernel-matrix path (tensor cores): a d = 32768 BF16 SPD matrix
     (2.1 GB), n = 30, M = 32.  The step streams B once: bytes per step =
@@ -579,7 +662,8 @@ def main():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint/forward (config 3) measurement")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) measurement")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core measurement")
-    ap.add_argument("--only", choices=["dense", "adjoint"], default=None,
+    ap.add_argument("--no-latency", action="store_true", help="skip the config-0 latency measurement")
+    ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency"], default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
     args = ap.parse_args()
