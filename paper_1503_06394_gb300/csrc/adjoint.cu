@@ -73,7 +73,8 @@ __device__ __forceinline__ void adj_reduce_scatter4(float (&dt)[4], int lig, uns
 // MODE 2: general.
 // MODE 3: final pass: H[pos(k,r)] += sum_p lambda_in[r,p] v[k,p]; no lambda_out.
 template <int MP, typename VT, int MODE>
-__global__ void __launch_bounds__(kThreads) adjoint_kernel(const AdjArgs args) {
+// 6 resident CTAs per SM (40 registers, no spills): the pass is latency bound.
+__global__ void __launch_bounds__(kThreads, 6) adjoint_kernel(const AdjArgs args) {
     constexpr int LPR = MP / 4;
     constexpr int GPW = 32 / LPR;
     constexpr int NW = MP <= 32 ? 1 : MP / 32;
@@ -213,6 +214,36 @@ __global__ void adjoint_gather_kernel(int64_t d, const int64_t* __restrict__ row
                 G[pos] = (float)(gscale * (double)H[hit]);
             }
         }
+    }
+}
+
+template <int MP, typename VT>
+static int adj_ctas_mp() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0) != cudaSuccess)
+        return 1;
+    return n > 0 ? n : 1;
+}
+
+template <typename VT>
+static int adj_ctas_vt(int panel) {
+    switch (panel) {
+        case 4: return adj_ctas_mp<4, VT>();
+        case 8: return adj_ctas_mp<8, VT>();
+        case 16: return adj_ctas_mp<16, VT>();
+        case 32: return adj_ctas_mp<32, VT>();
+        case 64: return adj_ctas_mp<64, VT>();
+        case 128: return adj_ctas_mp<128, VT>();
+        default: return 1;
+    }
+}
+
+int adjoint_ctas_per_sm(int panel, int dtype) {
+    switch (dtype) {
+        case 0: return adj_ctas_vt<float>(panel);
+        case 1: return adj_ctas_vt<bf16_t>(panel);
+        case 2: return adj_ctas_vt<double>(panel);
+        default: return 1;
     }
 }
 

@@ -821,6 +821,10 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         a.coeffs = at<double>(h, L.coeffs);
         a.prm = prm;
         a.mreal = mreal;
+        const int rows_per_cta = (kThreads / 32) * (128 / L.panel);
+        const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
+        const int64_t full = (int64_t)adjoint_ctas_per_sm(L.panel, (int)h->dtype) * h->sms;
+        const int agrid = (int)(need < full ? (need > 0 ? need : 1) : full);
         // lambda_i lives in lam[i % 3]
         for (int i = n; i >= 1; --i) {
             a.ci = i;
@@ -829,13 +833,13 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
             a.lam_prev = lam[(i + 2) % 3];
             a.w = i <= n - 1 ? wbuf(h, L, i, true) : nullptr;
             const int mode = i == n ? 0 : i == n - 1 ? 1 : 2;
-            CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, mode, L.grid, h->stream, a));
+            CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, mode, agrid, h->stream, a));
             ++launches;
         }
         a.lam_in = lam[1 % 3];  // lambda_1
         a.lam_out = nullptr;
         a.w = nullptr;
-        CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, 3, L.grid, h->stream, a));
+        CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, 3, agrid, h->stream, a));
         ++launches;
     }
     CUDA_TRY(launch_finalize(n, M, h->d, 0, prm, at<double>(h, L.T), at<double>(h, L.coeffs),

@@ -236,6 +236,7 @@ struct AdjArgs {
     int mreal;
 };
 cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a);
+int adjoint_ctas_per_sm(int panel, int dtype);
 cudaError_t launch_adjoint_gather(int64_t d, const int64_t* rowptr, const int32_t* col, const float* H,
                                   double gscale, float* G, uint32_t* flags, int grid, cudaStream_t s);
 
