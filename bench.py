@@ -345,7 +345,7 @@ def run_ours(args, rank, world):
             "b_gather_per_step": bg, "b_min_per_step": bmin,
             "effective_gbs_bmin": world * n * bmin / (ms_per_step / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(args, B),
+                         "frac": achieved / peak, "traffic": profiled_traffic(args, B, variant),
                          "kernel": "step_kernel (general recurrence step, j >= 2)",
                          "avg_launch_ms": kernel_avg_ms, "peak_source": peak_src},
             "gpu_launches": total_launches,
@@ -627,9 +627,10 @@ def dense_leg(args, torch):
             "kernel": "dense_step_kernel (tcgen05.mma kind::f16, TMA, TMEM)"}
 
 
-def profiled_traffic(args, B):
+def profiled_traffic(args, B, variant=None):
     """DRAM bytes (read + write) per general-step launch from the committed ncu
-    summary of this workload, if the step kernel's source is unchanged since."""
+    summary of this workload, if the step kernel's source and the inner-loop
+    variant are the ones it was captured with."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "step_kernel_config2_traffic.md")
@@ -640,6 +641,8 @@ def profiled_traffic(args, B):
     want = hashlib.sha256(open(src, "rb").read()).hexdigest()
     vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())
     if vals.get("step_kernel_sha256", "").strip() != want:
+        return None
+    if variant is not None and vals.get("variant", "").strip() != str(variant):
         return None
     try:
         return float(vals["traffic_bytes_per_launch"].strip())

@@ -263,7 +263,8 @@ CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
 
 /* Autotuner: times `reps` launches of the general recurrence step of every
  * variant on this matrix with M probes (workspace and interval must be set;
- * the workspace contents are overwritten) and keeps the fastest on the handle.
+ * the workspace contents are overwritten) and keeps the fastest on the handle
+ * (the current variant stays unless another is at least 2 % faster).
  * Returns the chosen variant and its mean step time in ms (either may be NULL).
  * Errors: CLD_ERR_INVALID, CLD_ERR_NOMEM, CLD_ERR_INTERVAL, CLD_ERR_CUDA. */
 CLD_API cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* ms_out);

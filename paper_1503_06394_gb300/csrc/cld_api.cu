@@ -1086,7 +1086,7 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     if (h->dense) return fail(CLD_ERR_UNSUPPORTED, "the dense path has a single kernel");
     const int saved = h->impl;
     int best = -1;
-    float best_ms = 0.f;
+    float best_ms = 0.f, saved_ms = -1.f;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -1134,6 +1134,7 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
         float ms = 0.f;
         CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         ms /= reps;
+        if (v == saved) saved_ms = ms;
         if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
     }
     cudaEventDestroy(e0);
@@ -1141,6 +1142,12 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     if (best < 0) {
         h->impl = saved;
         return fail(CLD_ERR_NOMEM, "workspace too small to time any variant");
+    }
+    // keep the current variant unless another is at least 2 % faster, so that
+    // timing noise does not flip the choice (and the summation order) run to run
+    if (saved_ms > 0.f && saved_ms <= 1.02f * best_ms) {
+        best = saved;
+        best_ms = saved_ms;
     }
     h->impl = best;
     if (variant_out) *variant_out = best;
