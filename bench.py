@@ -233,7 +233,8 @@ def run_only(args):
     import __graft_entry__
 
     __graft_entry__.build()
-    leg = {"dense": dense_leg, "adjoint": adjoint_leg, "paper": paper_leg, "latency": latency_leg}[args.only]
+    leg = {"dense": dense_leg, "adjoint": adjoint_leg, "paper": paper_leg, "latency": latency_leg,
+           "gmrf": gmrf_leg}[args.only]
     out = leg(args, torch, 1) if args.only == "adjoint" else leg(args, torch)
     print(json.dumps({"only": args.only, **out}), flush=True)
 
@@ -512,6 +513,65 @@ def batch_leg(args, torch):
     return out
 
 
+def gmrf_leg(args, torch):
+    """The paper's GMRF experiment (Sec. 5.2, Fig. 3): a sample x of the
+    4-neighbour GMRF on a 5000 x 5000 grid (d = 2.5e7) with partial
+    correlation rho = -0.22, drawn by a chequerboard Gibbs sampler
+    (x_i | rest ~ N(rho * sum of neighbours, 1)); then the log-likelihood
+    1/2 logdet J(rho) - 1/2 x^T J(rho) x over a grid of rho, logdet J(rho)
+    estimated on the GPU (n = 60, M = 16) and, for comparison, exact from the
+    separable spectrum 1 - rho (2 cos(pi i/(N+1)) + 2 cos(pi j/(N+1)))."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    N = int(round((args.d or 25_000_000) ** 0.5))
+    rho0, sweeps = -0.22, 200
+    g = torch.Generator(device="cuda").manual_seed(1007)
+    x = torch.zeros((N + 2, N + 2), dtype=torch.float64, device="cuda")  # zero halo
+    ii, jj = torch.meshgrid(torch.arange(N, device="cuda"), torch.arange(N, device="cuda"), indexing="ij")
+    colour = ((ii + jj) % 2).bool()
+    t0 = time.time()
+    for _ in range(sweeps):
+        for c in (False, True):
+            nb = x[:-2, 1:-1] + x[2:, 1:-1] + x[1:-1, :-2] + x[1:-1, 2:]
+            z = torch.randn((N, N), dtype=torch.float64, device="cuda", generator=g)
+            inner = x[1:-1, 1:-1]
+            inner[colour == c] = (rho0 * nb + z)[colour == c]
+    xs = x[1:-1, 1:-1].contiguous()
+    sum_sq = float((xs * xs).sum())
+    xax = float(2 * ((xs[:-1, :] * xs[1:, :]).sum() + (xs[:, :-1] * xs[:, 1:]).sum()))  # x^T A x
+    gibbs_s = time.time() - t0
+    del x, ii, jj, colour
+    J = workloads.gmrf_grid(N, 0.0)
+    rows = np.repeat(np.arange(J.d), np.diff(J.rowptr))
+    diag = torch.as_tensor(J.col == rows, device="cuda")
+    vals = torch.ones(J.nnz, dtype=torch.float32, device="cuda")
+    m = CsrLogdet(J.rowptr, J.col, vals)
+    n, M = 60, 16
+    c = np.cos(np.pi * np.arange(1, N + 1) / (N + 1))
+    sweep = []
+    t0 = time.time()
+    for rho in np.round(np.arange(-0.245, 0.0001, 0.005), 4):
+        m.val.copy_(torch.where(diag, 1.0, float(rho)).float())  # values of J(rho), same pattern
+        m.set_interval(1 - 4 * abs(rho) - 1e-6, 1 + 4 * abs(rho) + 1e-6)
+        r = m.estimate(n, M, 0)
+        mu = 1.0 - rho * 2.0 * (c[:, None] + c[None, :])
+        exact = float(np.sum(np.log(mu)))
+        quad = sum_sq - rho * xax
+        sweep.append({"rho": float(rho), "logdet": r["logdet"], "stderr": r["stderr"], "logdet_exact": exact,
+                      "loglik": 0.5 * r["logdet"] - 0.5 * quad, "loglik_exact": 0.5 * exact - 0.5 * quad})
+    sweep_s = time.time() - t0
+    m.close()
+    best = max(sweep, key=lambda e: e["loglik"])
+    best_exact = max(sweep, key=lambda e: e["loglik_exact"])
+    return {"workload": "GMRF grid %d x %d (d=%d, nnz=%d), Gibbs sample at rho=%g (%d sweeps), n=%d, M=%d" % (
+                N, N, J.d, J.nnz, rho0, sweeps, n, M),
+            "argmax_rho": best["rho"], "argmax_rho_exact_logdet": best_exact["rho"], "true_rho": rho0,
+            "gibbs_s": gibbs_s, "sweep_s": sweep_s, "estimates": len(sweep),
+            "max_rel_err_logdet": max(abs(e["logdet"] - e["logdet_exact"]) / abs(e["logdet_exact"])
+                                      for e in sweep if e["logdet_exact"] != 0),
+            "sweep": sweep}
+
+
 def paper_leg(args, torch):
     """The paper's timing experiment (Sec. 5.1, Fig. 1a): Algorithm 2 on its own
     sparse random generator (five U[-1,1] off-diagonals per row, mirrored,
@@ -666,7 +726,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) measurement")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core measurement")
     ap.add_argument("--no-latency", action="store_true", help="skip the config-0 latency measurement")
-    ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency"], default=None,
+    ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency", "gmrf"], default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
     args = ap.parse_args()

@@ -178,6 +178,17 @@ def grid_gmrf(N: int, kappa2: float) -> Csr:
                        "grid_gmrf(N=%d,kappa2=%g)" % (N, kappa2))
 
 
+def gmrf_grid(N: int, rho: float) -> Csr:
+    """Precision J = I - rho A of the 4-neighbour GMRF on an N x N grid (Sec.
+    5.2): unit diagonal, -rho between grid neighbours (partial correlation
+    rho), natural row-major order; SPD for |rho| < 1/4."""
+    G = grid_gmrf(N, 0.0)  # pattern: diagonal 4, neighbours -1
+    rows = np.repeat(np.arange(G.d), np.diff(G.rowptr))
+    G.val = np.where(G.col == rows, 1.0, rho)
+    G.name = "gmrf_grid(N=%d,rho=%g)" % (N, rho)
+    return G
+
+
 def nonsymmetric_dominant(d: int, picks: int, seed: int) -> Csr:
     rng = np.random.default_rng(seed)
     if d < 2 or picks <= 0:
