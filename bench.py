@@ -260,15 +260,23 @@ def run_ours(args, rank, world):
         m.auto_interval(0)
     else:
         m.set_interval(*interval)
-    variant, _ = m.autotune(n, M)
+    if args.variant is None:
+        variant, _ = m.autotune(n, M)
+    else:
+        variant = args.variant
+        m.set_kernel_variant(variant)
     m.reserve(n, M)
     bg, bmin, nnz_off = algorithmic_bytes_per_step(B, M, s_v)
+    # the grid stencil's neighbour rows are L2 hits (its roofline is B_min);
+    # uniformly random columns miss L2 (B_gather)
+    model = "B_min" if args.config == 1 else "B_gather"
+    bstep = bmin if args.config == 1 else bg
     peak, peak_src = read_peaks()
     with ClockSampler(local) as clk:
         ms_per_step, kernel_avg_ms, step_launches, total_launches, r_last = time_estimates(
             m, n, M, seed, interval, args.steps, args.warmup, torch, world)
-    value = world * n * bg / (ms_per_step / 1e3) / 1e9
-    achieved = bg / (kernel_avg_ms / 1e3) / 1e9
+    value = world * n * bstep / (ms_per_step / 1e3) / 1e9
+    achieved = bstep / (kernel_avg_ms / 1e3) / 1e9
     panel, lpr, ctas, threads = m.launch_config(M)
     a_e, b_e = (interval if interval is not None else Bd.cld_auto_interval(m.h, 0))
     rr = m.estimate(n, M, cfg["probe_seed"], details=True)
@@ -286,7 +294,8 @@ def run_ours(args, rank, world):
         if iv16 is None:
             iv16 = m16.auto_interval(0)
         m16.autotune(n, M)
-        bg16, _, _ = algorithmic_bytes_per_step(B, M, 2)
+        bg16, bmin16, _ = algorithmic_bytes_per_step(B, M, 2)
+        bg16 = bmin16 if args.config == 1 else bg16
         ms16, k16, _, _, _ = time_estimates(m16, n, M, seed, interval, args.steps, max(1, args.warmup - 1), torch, world)
         m16.set_interval(*iv16)
         r16 = m16.estimate(n, M, cfg["probe_seed"], details=True)
@@ -343,14 +352,14 @@ def run_ours(args, rank, world):
                                   "variant": variant}},
             "logdet": r_last["logdet"], "stderr": r_last["stderr"],
             "logdet_s": ms_per_step / 1e3, "pct_of_peak": 100.0 * value / world / peak,
-            "b_gather_per_step": bg, "b_min_per_step": bmin,
+            "bytes_model": model, "b_gather_per_step": bg, "b_min_per_step": bmin,
             "effective_gbs_bmin": world * n * bmin / (ms_per_step / 1e3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": profiled_traffic(args, B, variant),
                          "kernel": "step_kernel (general recurrence step, j >= 2)",
                          "avg_launch_ms": kernel_avg_ms, "peak_source": peak_src},
             "gpu_launches": total_launches,
-            "e2e": {"value": world * n * bg / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": world * n * bstep / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": 32, "seconds_per_step": e2e_s},
             "clocks": clk.summary(), "generation_s": gen_s}
     if bf16 is not None:
@@ -454,7 +463,9 @@ def batch_leg(args, torch):
     n, M = cfg["n"], cfg["M"]
     spd, gen = workloads.batch_mixed(cfg["count"], cfg["dmin"], cfg["dmax"], cfg["seed"])
     out = {"workload": "%d matrices, d log-uniform in [%g, %g] (sum d = %d), half SPD, half general; n=%d, M=%d" % (
-        cfg["count"], cfg["dmin"], cfg["dmax"], sum(m.d for m in spd + gen), n, M)}
+        cfg["count"], cfg["dmin"], cfg["dmax"], sum(m.d for m in spd + gen), n, M),
+           "gbs_model": "B_gather per block (no reuse); every block's w_j (<= 12.8 MB) fits in L2, so "
+                        "gathers mostly hit L2 and this effective rate can exceed the DRAM copy peak"}
     steps = max(1, args.steps)
     for dtype in ("f32", "bf16"):
         tot_ms, tot_bytes = 0.0, 0
@@ -481,7 +492,7 @@ def batch_leg(args, torch):
             nbytes = n * batch_bytes(mats, M, 2 if dtype == "bf16" else 4, kind == "general")
             out["%s_%s_ms" % (kind, dtype)] = ms
             out["%s_%s_gbs" % (kind, dtype)] = nbytes / (ms / 1e3) / 1e9
-            out["%s_variant" % kind] = v
+            out["%s_%s_variant" % (kind, dtype)] = v
             tot_ms += ms
             tot_bytes += nbytes
         out["batched_%s_ms" % dtype] = tot_ms
@@ -687,10 +698,10 @@ def dense_leg(args, torch):
             "kernel": "dense_step_kernel (tcgen05.mma kind::f16, TMA, TMEM)"}
 
 
-def profiled_traffic(args, B, variant=None):
-    """DRAM bytes (read + write) per general-step launch from the committed ncu
-    summary of this workload, if the step kernel's source and the inner-loop
-    variant are the ones it was captured with."""
+def profiled_traffic(args, B, variant):
+    """DRAM bytes (read + write) per general-step launch of inner-loop variant
+    ``variant`` from the committed ncu summary of this workload, if the step
+    kernel's source is the one it was captured with."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "step_kernel_config2_traffic.md")
@@ -702,10 +713,8 @@ def profiled_traffic(args, B, variant=None):
     vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())
     if vals.get("step_kernel_sha256", "").strip() != want:
         return None
-    if variant is not None and vals.get("variant", "").strip() != str(variant):
-        return None
     try:
-        return float(vals["traffic_bytes_per_launch"].strip())
+        return float(vals["traffic_bytes_per_launch_v%d" % variant].strip())
     except (KeyError, ValueError):
         return None
 
@@ -729,6 +738,8 @@ def main():
     ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency", "gmrf"], default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4],
+                    help="pin the recurrence-step inner-loop variant instead of autotuning it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

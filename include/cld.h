@@ -254,10 +254,17 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *   0: each lane loads 4 (column, value) pairs itself, 4 row gathers in flight;
  *   1: the lanes of a row load 8 pairs cooperatively and issue 8 row gathers
  *      back to back, the next chunk's pairs loaded ahead (default);
- *   2: as 1 with chunks of 4 pairs (fewer registers, more resident CTAs).
- * The default at creation is 2 when the matrix holds >= 8 stored entries per
- * row on average, else 0.  The variant also sets the grid size, so the last
- * bits of the moments (their summation order) can change with it.
+ *   2: as 1 with chunks of 4 pairs (fewer registers, more resident CTAs);
+ *   3: a shared-memory ring: the rows of w_j gathered by a row's first 5
+ *      entries, its own row and its row of w_{j-1} are copied into shared
+ *      memory with cp.async while the group consumes the previous row (for
+ *      short rows, e.g. stencils, where dependent loads otherwise serialise);
+ *      entries past the 5th are gathered directly;
+ *   4: as 3 with the first 8 entries staged (more shared memory, 2 CTAs/SM).
+ * The default at creation is 3 when the matrix holds at most 6 stored entries
+ * per row on average, else 4 (batches: 0).  The variant also sets the grid
+ * size, so the last bits of the moments (their summation order) can change
+ * with it.
  * Errors: CLD_ERR_INVALID for an unknown variant. */
 CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
 

@@ -15,10 +15,10 @@
 namespace cld {
 
 template <int MP, typename VT, int GATHER, int PREV, int IMPL>
-__global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) batch_step_kernel(const BatchStepArgs ba) {
+__global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value))
+    batch_step_kernel(const BatchStepArgs ba) {
     constexpr int LPR = MP / 4;
     constexpr int GPW = 32 / LPR;
-    constexpr int NW = MP <= 32 ? 1 : MP / 32;
     constexpr int WPB = kThreads / 32;
     const StepArgs& args = ba.s;
     const int lane = threadIdx.x & 31;
@@ -33,26 +33,23 @@ __global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) batch_st
                                     p0 + 2 < args.mreal ? 1.f : 0.f, p0 + 3 < args.mreal ? 1.f : 0.f);
     const VT* __restrict__ val = static_cast<const VT*>(args.val);
     __shared__ double red[WPB][MP];
+    extern __shared__ float4 ring[];
 
     for (int64_t t = blockIdx.x; t < ba.ntiles; t += gridDim.x) {
         const Tile tl = ba.tiles[t];
         const Params* P = ba.bprm + tl.blk;
         const float scale = P->scale_hi, scale_lo = P->scale_lo, shift = P->shift_hi, shift_lo = P->shift_lo;
         float4 tacc = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int64_t row = tl.lo + gloc; row < tl.hi; row += gcta) {
-            const int64_t k0 = __ldg(args.rowptr + row), k1 = __ldg(args.rowptr + row + 1);
-            const float4 acc = row_product<MP, GATHER, IMPL>(k0, k1, args.col, val, args.x, args.vbits, lig, p0,
-                                                             wsel, bsh, mask, gmask);
-            const float4 v = signs4(__ldg(args.vbits + row * NW + wsel), bsh, mask);
-            const float4 own = (PREV == 0) ? v : ldg4(args.own + row * MP + p0);
-            const float4 pv = (PREV == 2) ? ldcs4(args.wprev + row * MP + p0) : v;
-            const float4 res = recurrence_update<PREV>(acc, own, pv, scale, scale_lo, shift, shift_lo);
-            tacc.x = fmaf(v.x, res.x, tacc.x);
-            tacc.y = fmaf(v.y, res.y, tacc.y);
-            tacc.z = fmaf(v.z, res.z, tacc.z);
-            tacc.w = fmaf(v.w, res.w, tacc.w);
+        auto finish = [&](int64_t row, const float4& acc, const RowOperands& o) {
+            const float4 res = recurrence_update<PREV>(acc, o.own, o.pv, scale, scale_lo, shift, shift_lo);
+            tacc.x = fmaf(o.v.x, res.x, tacc.x);
+            tacc.y = fmaf(o.v.y, res.y, tacc.y);
+            tacc.z = fmaf(o.v.z, res.z, tacc.z);
+            tacc.w = fmaf(o.v.w, res.w, tacc.w);
             st4(args.out + row * MP + p0, res);
-        }
+        };
+        rows_all<MP, GATHER, PREV, 1, IMPL>(args, val, tl.lo + gloc, tl.hi, gcta, lig, p0, wsel, bsh, mask, gmask,
+                                            ring, finish);
         double t0 = tacc.x, t1 = tacc.y, t2 = tacc.z, t3 = tacc.w;
 #pragma unroll
         for (int off = LPR; off < 32; off <<= 1) {
@@ -78,16 +75,25 @@ __global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) batch_st
     }
 }
 
+template <int MP, typename VT, int GATHER, int PREV, int IMPL>
+static cudaError_t launch_one_batch(int grid, cudaStream_t s, const BatchStepArgs& a) {
+    constexpr auto kern = batch_step_kernel<MP, VT, GATHER, PREV, IMPL>;
+    constexpr int smem = step_smem<IMPL, GATHER>();
+    cudaError_t e = smem_opt_in<kern>(smem);
+    if (e != cudaSuccess || grid == 0) return e;  // grid 0: opt in only
+    kern<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MP, typename VT, int IMPL>
 static cudaError_t launch_batch_impl(StepKind kind, int grid, cudaStream_t s, const BatchStepArgs& a) {
     switch (kind) {
-        case kStepFirst: batch_step_kernel<MP, VT, 1, 0, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepSecond: batch_step_kernel<MP, VT, 0, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepGeneral: batch_step_kernel<MP, VT, 0, 2, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepFirstFromFloat: batch_step_kernel<MP, VT, 0, 0, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepFirst: return launch_one_batch<MP, VT, 1, 0, IMPL>(grid, s, a);
+        case kStepSecond: return launch_one_batch<MP, VT, 0, 1, IMPL>(grid, s, a);
+        case kStepGeneral: return launch_one_batch<MP, VT, 0, 2, IMPL>(grid, s, a);
+        case kStepFirstFromFloat: return launch_one_batch<MP, VT, 0, 0, IMPL>(grid, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <int MP, typename VT>
@@ -96,6 +102,8 @@ static cudaError_t launch_batch_mp(StepKind kind, int grid, cudaStream_t s, cons
         case 0: return launch_batch_impl<MP, VT, 0>(kind, grid, s, a);
         case 1: return launch_batch_impl<MP, VT, 1>(kind, grid, s, a);
         case 2: return launch_batch_impl<MP, VT, 2>(kind, grid, s, a);
+        case 3: return launch_batch_impl<MP, VT, 3>(kind, grid, s, a);
+        case 4: return launch_batch_impl<MP, VT, 4>(kind, grid, s, a);
         default: return cudaErrorInvalidValue;
     }
 }

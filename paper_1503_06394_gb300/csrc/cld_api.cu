@@ -117,6 +117,10 @@ struct Layout {
     int panel, nw, grid, ggrid;
 };
 
+// Inner-loop variant at creation: the shared-memory rings (3 stages the
+// first 5 entries of a row, 4 the first 8).
+static int default_impl(int64_t d, int64_t nnz) { return nnz <= 6 * d ? 3 : 4; }
+
 static int panel_for_dense(int M) { return M <= 32 ? 32 : M <= 64 ? 64 : 128; }
 
 static int panel_for(int M) {
@@ -506,6 +510,19 @@ static cld_status run_graph(cld_ctx* h, long long kind, int n, int M, F&& enqueu
             h->gexec = nullptr;
         }
         if (!h->cap_stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        // kernel attributes (shared-memory opt-in of the ring variants) are set
+        // outside the capture
+        if (!h->dense) {
+            StepArgs a{};
+            a.impl = h->impl;
+            BatchStepArgs b{};
+            b.s.impl = h->impl;
+            for (int k = kStepFirst; k <= kStepFirstFromFloat; ++k) {
+                CUDA_TRY(launch_step(panel_for(M), (int)h->dtype, (StepKind)k, 0, h->stream, a));
+                if (h->nb > 0 && k != kProdBits && k != kProdFloat)
+                    CUDA_TRY(launch_batch_step(panel_for(M), (int)h->dtype, (StepKind)k, 0, h->stream, b));
+            }
+        }
         // order the capture after work already queued on the user's stream
         cudaStream_t user = h->stream;
         const bool prof = h->profiling;
@@ -586,7 +603,7 @@ cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t
     // Default inner loop: cooperative 4-entry chunks pay off once rows hold
     // about 8 or more stored entries (measured on GB300: random SPD with 11
     // entries per row 3.22 vs 3.27 ms per step; 5-point grid 0.32 vs 0.22 ms).
-    h->impl = (d > 0 && nnz >= 8 * d) ? 2 : 0;
+    h->impl = default_impl(d, nnz);
     if (cudaGetDevice(&h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
         delete h;
@@ -872,6 +889,7 @@ cld_status cld_host_workspace_size(int64_t d, int64_t nnz, cld_dtype val_dtype, 
         return fail(CLD_ERR_INVALID, "unknown value dtype");
     cld_ctx tmp;
     tmp.d = d; tmp.nnz = nnz; tmp.dtype = val_dtype; tmp.kind = CLD_GENERAL;  // largest layout
+    tmp.impl = default_impl(d, nnz);
     if (cudaGetDevice(&tmp.device) != cudaSuccess ||
         cudaDeviceGetAttribute(&tmp.sms, cudaDevAttrMultiProcessorCount, tmp.device) != cudaSuccess)
         return fail(CLD_ERR_CUDA, "no CUDA device");

@@ -125,15 +125,17 @@ struct StepArgs {
     double* tpart;           // [grid][panel] partial moments (epi 1)
     const Params* prm;
     int mreal;               // real probes in this panel
-    int impl;                // inner-loop variant (0 or 1, see step_kernel.cuh)
+    int impl;                // inner-loop variant (0..kNumStepImpls-1, see step_kernel.cuh)
 };
 
-constexpr int kNumStepImpls = 3;
+constexpr int kNumStepImpls = 5;
 
 enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
                 kStepFirstFromFloat = 5 };
 
 // Launches one step with `grid` CTAs on `stream`.  panel in {4,8,...,128}.
+// grid 0 launches nothing and only sets the kernel's shared-memory attribute
+// on the current device (done before a stream capture).
 cudaError_t launch_step(int panel, int dtype, StepKind kind, int grid, cudaStream_t stream,
                         const StepArgs& a);
 // Resident CTAs per SM of the general step kernel (for grid sizing).

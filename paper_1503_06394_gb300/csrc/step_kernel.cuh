@@ -21,6 +21,8 @@
 // sums the partials over CTAs in a fixed order, so results are deterministic.
 #pragma once
 
+#include <atomic>
+
 #include "cld_internal.cuh"
 
 namespace cld {
@@ -34,108 +36,149 @@ __device__ __forceinline__ float4 ldcs4(const float* p) {
 __device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
 
 
+// Column indices and values of the chunk of CH stored entries starting at kb
+// (entries at or beyond k1 read as column 0, value 0), spread over the LPR
+// lanes of a row's group: lane lig holds entries e * LPR + lig, e < E.  CSR
+// streams are read with the evict-first policy so they do not displace
+// gathered rows of w_j from L2.
+template <int CH, int E, int LPR, typename VT>
+__device__ __forceinline__ void load_chunk(int64_t kb, int64_t k1, const int32_t* __restrict__ col,
+                                           const VT* __restrict__ val, int lig, int (&cr)[E], float (&vr)[E]) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int idx = e * LPR + lig;  // entry of the chunk this lane loads
+        const int64_t k = kb + idx;
+        const bool ok = idx < CH && k < k1;
+        cr[e] = ok ? __ldcs(col + k) : 0;
+        vr[e] = ok ? load_val_cs(val + k) : 0.f;
+    }
+}
+
+// Row product over [k0, k1) in chunks of CH entries whose first chunk is
+// already in (creg, vreg): the pairs are broadcast with group-masked shuffles,
+// all CH row gathers are issued back to back, and the next chunk's pairs are
+// loaded before the current chunk's gathers are consumed.
+template <int MP, int GATHER, int CH, int E, typename VT>
+__device__ __forceinline__ float4 chunk_product(int64_t k0, int64_t k1, int (&creg)[E], float (&vreg)[E],
+                                                const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                const float* __restrict__ x, const uint32_t* __restrict__ vbits,
+                                                int lig, int p0, int wsel, int bsh, float4 mask, unsigned gmask) {
+    constexpr int LPR = MP / 4;
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    int cnext[E];
+    float vnext[E];
+    for (int64_t k = k0; k < k1; k += CH) {
+        if (k + CH < k1) load_chunk<CH, E, LPR>(k + CH, k1, col, val, lig, cnext, vnext);
+        float4 xv[CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int c = __shfl_sync(gmask, creg[u / LPR], u % LPR, LPR);
+            if (k + u < k1) {
+                if (GATHER == 1)
+                    xv[u] = signs4(__ldg(vbits + (int64_t)c * NW + wsel), bsh, mask);
+                else
+                    xv[u] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)c * MP + p0));
+            } else {
+                xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const float av = __shfl_sync(gmask, vreg[u / LPR], u % LPR, LPR);
+            acc.x = fmaf(av, xv[u].x, acc.x);
+            acc.y = fmaf(av, xv[u].y, acc.y);
+            acc.z = fmaf(av, xv[u].z, acc.z);
+            acc.w = fmaf(av, xv[u].w, acc.w);
+        }
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            creg[e] = cnext[e];
+            vreg[e] = vnext[e];
+        }
+    }
+    return acc;
+}
+
+// Entries per chunk of the cooperative variants (1: 8, 2: 4).
+template <int IMPL>
+struct ChunkSize { static constexpr int value = IMPL == 2 ? 4 : 8; };
+
+// acc += sum over the stored entries [k0, k1) of one row, in entry order:
+// each lane loads the (index, value) pairs of 4 entries at a time itself, then
+// gathers those 4 rows (4 gathers in flight per group).  The whole row product
+// of variant 0, and the entries past the staged chunk of the ring variants.
+template <int MP, int GATHER, typename VT>
+__device__ __forceinline__ float4 tail_product(float4 acc, int64_t k0, int64_t k1, const int32_t* __restrict__ col,
+                                               const VT* __restrict__ val, const float* __restrict__ x,
+                                               const uint32_t* __restrict__ vbits, int p0, int wsel, int bsh,
+                                               float4 mask) {
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    constexpr int U = 4;
+    for (int64_t k = k0; k < k1; k += U) {
+        int c[U];
+        float a[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const bool ok = k + u < k1;
+            c[u] = ok ? __ldg(col + k + u) : -1;
+            a[u] = ok ? load_val(val + k + u) : 0.f;
+        }
+        float4 xv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (c[u] >= 0) {
+                if (GATHER == 1)
+                    xv[u] = signs4(__ldg(vbits + (int64_t)c[u] * NW + wsel), bsh, mask);
+                else
+                    xv[u] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)c[u] * MP + p0));
+            } else {
+                xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            acc.x = fmaf(a[u], xv[u].x, acc.x);
+            acc.y = fmaf(a[u], xv[u].y, acc.y);
+            acc.z = fmaf(a[u], xv[u].z, acc.z);
+            acc.w = fmaf(a[u], xv[u].w, acc.w);
+        }
+    }
+    return acc;
+}
+
 // Row product acc = sum_k X[row, k] * x[k, p0..p0+3] over the stored entries
 // [k0, k1) of one row, for the four probes of this lane.
 //
-// IMPL 0: each lane loads the column index and value of 4 entries at a time
-//         itself, then gathers those 4 rows (4 gathers in flight per group).
+// IMPL 0: tail_product over the whole row.
 // IMPL 1 (2): the LPR lanes of the group load the next 8 (4) (index, value) pairs
-//         cooperatively (one coalesced access per lane), broadcast them with
-//         shuffles and issue all 8 (4) row gathers back to back; the indices of the
-//         following chunk are loaded before the current chunk's gathers are
-//         consumed.  CSR streams are read with the evict-first policy so they
-//         do not displace gathered rows of w_j from L2.
+//         cooperatively (one coalesced access per lane) and chunk_product
+//         consumes them.
+// IMPL 3 and 4 (the shared-memory ring) do not go through row_product for
+// float gathers; see rows_ring.
 //
-// The shuffles of IMPL 1/2 name only the LPR lanes of the row's group
-// (gmask): groups of one warp own rows of different lengths, so their chunk
-// loops (and the last grid-stride round) diverge, and a full-warp mask would be
-// undefined there.
+// The shuffles of the cooperative variants name only the LPR lanes of the
+// row's group (gmask): groups of one warp own rows of different lengths, so
+// their chunk loops (and the last grid-stride round) diverge, and a full-warp
+// mask would be undefined there.
 template <int MP, int GATHER, int IMPL, typename VT>
 __device__ __forceinline__ float4 row_product(int64_t k0, int64_t k1, const int32_t* __restrict__ col,
                                               const VT* __restrict__ val, const float* __restrict__ x,
                                               const uint32_t* __restrict__ vbits, int lig, int p0,
                                               int wsel, int bsh, float4 mask, unsigned gmask) {
     constexpr int LPR = MP / 4;
-    constexpr int NW = MP <= 32 ? 1 : MP / 32;
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (IMPL == 0) {
-        constexpr int U = 4;
-        for (int64_t k = k0; k < k1; k += U) {
-            int c[U];
-            float a[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = k + u < k1;
-                c[u] = ok ? __ldg(col + k + u) : -1;
-                a[u] = ok ? load_val(val + k + u) : 0.f;
-            }
-            float4 xv[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (c[u] >= 0) {
-                    if (GATHER == 1)
-                        xv[u] = signs4(__ldg(vbits + (int64_t)c[u] * NW + wsel), bsh, mask);
-                    else
-                        xv[u] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)c[u] * MP + p0));
-                } else {
-                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                acc.x = fmaf(a[u], xv[u].x, acc.x);
-                acc.y = fmaf(a[u], xv[u].y, acc.y);
-                acc.z = fmaf(a[u], xv[u].z, acc.z);
-                acc.w = fmaf(a[u], xv[u].w, acc.w);
-            }
-        }
+    if constexpr (IMPL == 0) {
+        return tail_product<MP, GATHER>(make_float4(0.f, 0.f, 0.f, 0.f), k0, k1, col, val, x, vbits, p0, wsel, bsh,
+                                        mask);
     } else {
-        constexpr int CH = IMPL == 1 ? 8 : 4;        // entries per chunk
+        constexpr int CH = ChunkSize<IMPL>::value;
         constexpr int E = LPR >= CH ? 1 : CH / LPR;  // entries held per lane
-        int creg[E], cnext[E];
-        float vreg[E], vnext[E];
-        auto load_chunk = [&](int64_t kb, int* cr, float* vr) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int idx = e * LPR + lig;  // entry of the chunk this lane loads
-                const int64_t k = kb + idx;
-                const bool ok = idx < CH && k < k1;
-                cr[e] = ok ? __ldcs(col + k) : 0;
-                vr[e] = ok ? load_val_cs(val + k) : 0.f;
-            }
-        };
-        load_chunk(k0, creg, vreg);
-        for (int64_t k = k0; k < k1; k += CH) {
-            if (k + CH < k1) load_chunk(k + CH, cnext, vnext);
-            float4 xv[CH];
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                const int c = __shfl_sync(gmask, creg[u / LPR], u % LPR, LPR);
-                if (k + u < k1) {
-                    if (GATHER == 1)
-                        xv[u] = signs4(__ldg(vbits + (int64_t)c * NW + wsel), bsh, mask);
-                    else
-                        xv[u] = __ldg(reinterpret_cast<const float4*>(x + (int64_t)c * MP + p0));
-                } else {
-                    xv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < CH; ++u) {
-                const float av = __shfl_sync(gmask, vreg[u / LPR], u % LPR, LPR);
-                acc.x = fmaf(av, xv[u].x, acc.x);
-                acc.y = fmaf(av, xv[u].y, acc.y);
-                acc.z = fmaf(av, xv[u].z, acc.z);
-                acc.w = fmaf(av, xv[u].w, acc.w);
-            }
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                creg[e] = cnext[e];
-                vreg[e] = vnext[e];
-            }
-        }
+        int creg[E];
+        float vreg[E];
+        load_chunk<CH, E, LPR>(k0, k1, col, val, lig, creg, vreg);
+        return chunk_product<MP, GATHER, CH, E>(k0, k1, creg, vreg, col, val, x, vbits, lig, p0, wsel, bsh, mask,
+                                                gmask);
     }
-    return acc;
 }
 
 // GATHER: 0 float rows of args.x, 1 probe signs.  PREV: 0 none, 1 v, 2 args.wprev.
@@ -161,18 +204,262 @@ __device__ __forceinline__ float4 recurrence_update(float4 acc, float4 own, floa
     return r;
 }
 
-// Resident-CTA targets per variant (256 threads): 6 (40 registers), 3, 4.
+// Epilogue operands of one row that do not depend on its gathers: the signs
+// v of the row, w_j's own row ("own"; v when PREV is 0) and w_{j-1} ("pv";
+// v when PREV is 0 or 1).
+struct RowOperands {
+    float4 v, own, pv;
+};
+
+template <int MP, int PREV, int EPI>
+__device__ __forceinline__ RowOperands row_operands(const StepArgs& args, int64_t row, int p0, int wsel, int bsh,
+                                                    float4 mask) {
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    RowOperands o;
+    if (EPI == 0) {
+        o.v = o.own = o.pv = make_float4(0.f, 0.f, 0.f, 0.f);
+        return o;
+    }
+    o.v = signs4(__ldg(args.vbits + row * NW + wsel), bsh, mask);
+    o.own = (PREV == 0) ? o.v : ldg4(args.own + row * MP + p0);
+    o.pv = (PREV == 2) ? ldcs4(args.wprev + row * MP + p0) : o.v;
+    return o;
+}
+
+// Rows first, first + stride, ... below end, one per group (variants 0-2):
+// each row's pointers (IMPL 1/2: loaded one row ahead), its product, then its
+// epilogue operands and finish(row, acc, operands).
+template <int MP, int GATHER, int PREV, int EPI, int IMPL, typename VT, class Finish>
+__device__ __forceinline__ void rows_plain(const StepArgs& args, const VT* __restrict__ val, int64_t first,
+                                           int64_t end, int64_t stride, int lig, int p0, int wsel, int bsh,
+                                           float4 mask, unsigned gmask, Finish&& finish) {
+    const int64_t* __restrict__ rowptr = args.rowptr;
+    int64_t k0 = 0, k1 = 0;
+    if (IMPL != 0 && first < end) {
+        k0 = __ldg(rowptr + first);
+        k1 = __ldg(rowptr + first + 1);
+    }
+    for (int64_t row = first; row < end; row += stride) {
+        float4 acc;
+        if (IMPL == 0) {
+            k0 = __ldg(rowptr + row);
+            k1 = __ldg(rowptr + row + 1);
+            acc = row_product<MP, GATHER, IMPL>(k0, k1, args.col, val, args.x, args.vbits, lig, p0, wsel, bsh, mask,
+                                                gmask);
+        } else {
+            // row pointers of this group's next row, loaded ahead
+            int64_t n0 = 0, n1 = 0;
+            if (row + stride < end) {
+                n0 = __ldg(rowptr + row + stride);
+                n1 = __ldg(rowptr + row + stride + 1);
+            }
+            acc = row_product<MP, GATHER, IMPL>(k0, k1, args.col, val, args.x, args.vbits, lig, p0, wsel, bsh, mask,
+                                                gmask);
+            k0 = n0;
+            k1 = n1;
+        }
+        finish(row, acc, row_operands<MP, PREV, EPI>(args, row, p0, wsel, bsh, mask));
+    }
+}
+
+// ---------------------------------------------------------------- ring
+// Variants 3 and 4 stage the operands of a row in shared memory with
+// cp.async (16 bytes per lane per row: the lane's four probes) instead of
+// holding loads in flight in registers, so a group keeps the next row's
+// gathers in flight while it consumes the current one without the register
+// cost that would lower occupancy.  Per group and row: the first RC stored
+// entries' rows of w_j, w_j's own row and w_{j-1}'s row go to one of two
+// stages; entries past RC are gathered directly (tail_product, same order).
 template <int IMPL>
-struct StepOccupancy { static constexpr int value = IMPL == 0 ? 6 : IMPL == 1 ? 3 : 4; };
+struct RingChunk { static constexpr int value = IMPL == 3 ? 5 : 8; };
+
+// Dynamic shared memory of the ring variants (two stages of RC + 2 slots of
+// 16 bytes per thread); 0 for the others.
+__host__ __device__ constexpr int ring_bytes(int impl) {
+    return impl == 3 ? 2 * (5 + 2) * kThreads * 16 : impl == 4 ? 2 * (8 + 2) * kThreads * 16 : 0;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Rows first, first + stride, ... below end through the ring.  At the top
+// of the iteration for row r the copies of r are in flight or done, the pairs
+// and sign word of r + stride are in registers and the pointers of
+// r + 2 stride too; the iteration issues the copies of r + stride, loads the
+// pairs of r + 2 stride, waits for r's copies (leaving r + stride's in
+// flight), and consumes r.  Each thread reads only the slots it copied, so
+// its own cp.async.wait_group orders them; a slot is rewritten only by the
+// same thread after its value was consumed (in-order issue).
+template <int MP, int PREV, int EPI, int RC, typename VT, class Finish>
+__device__ __forceinline__ void rows_ring(const StepArgs& args, const VT* __restrict__ val, int64_t first,
+                                          int64_t end, int64_t stride, int lig, int p0, int wsel, int bsh,
+                                          float4 mask, unsigned gmask, float4* ring, Finish&& finish) {
+    constexpr int LPR = MP / 4;
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    constexpr int E = (RC + LPR - 1) / LPR;  // staged entries whose pairs a lane holds
+    constexpr int SL = RC + 2;               // slots per stage
+    constexpr bool kOwn = EPI == 1 && PREV != 0;
+    constexpr bool kPrev = PREV == 2;
+    const int64_t* __restrict__ rowptr = args.rowptr;
+    auto slot = [&](int st, int q) -> float4* { return ring + (st * SL + q) * kThreads + threadIdx.x; };
+    auto issue = [&](int st, int64_t row, int64_t k0, int64_t k1, const int (&cr)[E]) {
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+            const int c = __shfl_sync(gmask, cr[q / LPR], q % LPR, LPR);
+            if (k0 + q < k1) cp_async16(slot(st, q), args.x + (int64_t)c * MP + p0);
+        }
+        if (kOwn) cp_async16(slot(st, RC), args.own + row * MP + p0);
+        if (kPrev) cp_async16(slot(st, RC + 1), args.wprev + row * MP + p0);
+    };
+    int64_t k0 = 0, k1 = 0, n0 = 0, n1 = 0, m0 = 0, m1 = 0;
+    int cr[E], cn[E];
+    float vr[E], vn[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        cr[e] = cn[e] = 0;
+        vr[e] = vn[e] = 0.f;
+    }
+    uint32_t wr = 0, wn = 0;
+    if (first < end) {
+        k0 = __ldg(rowptr + first);
+        k1 = __ldg(rowptr + first + 1);
+        load_chunk<RC, E, LPR>(k0, k1, args.col, val, lig, cr, vr);
+        if (EPI == 1) wr = __ldg(args.vbits + first * NW + wsel);
+        issue(0, first, k0, k1, cr);
+        if (first + stride < end) {
+            n0 = __ldg(rowptr + first + stride);
+            n1 = __ldg(rowptr + first + stride + 1);
+            load_chunk<RC, E, LPR>(n0, n1, args.col, val, lig, cn, vn);
+            if (EPI == 1) wn = __ldg(args.vbits + (first + stride) * NW + wsel);
+            if (first + 2 * stride < end) {
+                m0 = __ldg(rowptr + first + 2 * stride);
+                m1 = __ldg(rowptr + first + 2 * stride + 1);
+            }
+        }
+    }
+    cp_async_commit();
+    int st = 0;
+    for (int64_t r = first; r < end; r += stride, st ^= 1) {
+        const int64_t nr = r + stride;
+        if (nr < end) issue(st ^ 1, nr, n0, n1, cn);
+        cp_async_commit();
+        int c2[E];
+        float v2[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            c2[e] = 0;
+            v2[e] = 0.f;
+        }
+        uint32_t w2 = 0;
+        int64_t q0 = 0, q1 = 0;
+        if (nr + stride < end) {
+            load_chunk<RC, E, LPR>(m0, m1, args.col, val, lig, c2, v2);
+            if (EPI == 1) w2 = __ldg(args.vbits + (nr + stride) * NW + wsel);
+            if (nr + 2 * stride < end) {
+                q0 = __ldg(rowptr + nr + 2 * stride);
+                q1 = __ldg(rowptr + nr + 2 * stride + 1);
+            }
+        }
+        cp_async_wait<1>();
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < RC; ++q) {
+            const float av = __shfl_sync(gmask, vr[q / LPR], q % LPR, LPR);
+            if (k0 + q < k1) {
+                const float4 xv = *slot(st, q);
+                acc.x = fmaf(av, xv.x, acc.x);
+                acc.y = fmaf(av, xv.y, acc.y);
+                acc.z = fmaf(av, xv.z, acc.z);
+                acc.w = fmaf(av, xv.w, acc.w);
+            }
+        }
+        if (k0 + RC < k1)
+            acc = tail_product<MP, 0>(acc, k0 + RC, k1, args.col, val, args.x, args.vbits, p0, wsel, bsh, mask);
+        RowOperands o;
+        if (EPI == 0) {
+            o.v = o.own = o.pv = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else {
+            o.v = signs4(wr, bsh, mask);
+            o.own = kOwn ? *slot(st, RC) : o.v;
+            o.pv = kPrev ? *slot(st, RC + 1) : o.v;
+        }
+        finish(r, acc, o);
+        k0 = n0;
+        k1 = n1;
+        n0 = m0;
+        n1 = m1;
+        m0 = q0;
+        m1 = q1;
+        wr = wn;
+        wn = w2;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            vr[e] = vn[e];
+            cn[e] = c2[e];
+            vn[e] = v2[e];
+        }
+    }
+    cp_async_wait<0>();
+}
+
+// The row loop of variant IMPL; sign gathers (GATHER 1) of the ring variants
+// take variant 0's loop.
+template <int MP, int GATHER, int PREV, int EPI, int IMPL, typename VT, class Finish>
+__device__ __forceinline__ void rows_all(const StepArgs& args, const VT* __restrict__ val, int64_t first,
+                                         int64_t end, int64_t stride, int lig, int p0, int wsel, int bsh,
+                                         float4 mask, unsigned gmask, float4* ring, Finish&& finish) {
+    if constexpr (IMPL >= 3 && GATHER == 0)
+        rows_ring<MP, PREV, EPI, RingChunk<IMPL>::value>(args, val, first, end, stride, lig, p0, wsel, bsh, mask,
+                                                         gmask, ring, finish);
+    else
+        rows_plain<MP, GATHER, PREV, EPI, (IMPL >= 3 ? 0 : IMPL)>(args, val, first, end, stride, lig, p0, wsel, bsh,
+                                                                  mask, gmask, finish);
+}
+
+// Resident-CTA targets per variant (256 threads): 6 (40 registers), 3, 4;
+// the ring variants are bounded by their shared memory (3 and 2 CTAs).
+// Sign gathers (GATHER 1) of the ring variants run variant 0's loop and target.
+template <int IMPL, int GATHER = 0>
+struct StepOccupancy {
+    static constexpr int I = (IMPL >= 3 && GATHER == 1) ? 0 : IMPL;
+    static constexpr int value = I == 0 ? 6 : I == 1 ? 3 : I == 2 ? 4 : I == 3 ? 3 : 2;
+};
+
+// Dynamic shared memory of one instantiation.
+template <int IMPL, int GATHER>
+constexpr int step_smem() { return (IMPL >= 3 && GATHER == 0) ? ring_bytes(IMPL) : 0; }
+
+// Opts kernel K into `bytes` of dynamic shared memory on the current device,
+// once per device (the attribute is per device; ordinals >= 64 set it on
+// every call).  Needed above 48 KB, before the first launch or occupancy query.
+template <auto K>
+cudaError_t smem_opt_in(int bytes) {
+    if (bytes <= 48 * 1024) return cudaSuccess;
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit != 0 && (done.load(std::memory_order_acquire) & bit) != 0) return cudaSuccess;
+    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit != 0) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
-__global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_kernel(const StepArgs args);
+__global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value)) step_kernel(const StepArgs args);
 
 template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
-__global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_kernel(const StepArgs args) {
+__global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value)) step_kernel(const StepArgs args) {
     constexpr int LPR = MP / 4;          // lanes per row
     constexpr int GPW = 32 / LPR;        // rows per warp
-    constexpr int NW = MP <= 32 ? 1 : MP / 32;
     constexpr int WPB = kThreads / 32;
 
     const int lane = threadIdx.x & 31;
@@ -181,18 +468,13 @@ __global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_ker
     const int g_in_w = lane / LPR;
     const int64_t gid = ((int64_t)blockIdx.x * WPB + warp) * GPW + g_in_w;
     const int64_t ngroups = (int64_t)gridDim.x * WPB * GPW;
-    const int64_t d = args.d;
 
     const int p0 = 4 * lig;
     const int wsel = p0 >> 5;
     const int bsh = p0 & 31;
     const float4 mask = make_float4(p0 < args.mreal ? 1.f : 0.f, p0 + 1 < args.mreal ? 1.f : 0.f,
                                     p0 + 2 < args.mreal ? 1.f : 0.f, p0 + 3 < args.mreal ? 1.f : 0.f);
-
-    const int64_t* __restrict__ rowptr = args.rowptr;
-    const int32_t* __restrict__ col = args.col;
     const VT* __restrict__ val = static_cast<const VT*>(args.val);
-    const uint32_t* __restrict__ vbits = args.vbits;
 
     float scale = 1.f, scale_lo = 0.f, shift = 0.f, shift_lo = 0.f;
     if (EPI == 1) {
@@ -203,45 +485,23 @@ __global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_ker
     }
 
     float4 tacc = make_float4(0.f, 0.f, 0.f, 0.f);
-
     const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g_in_w * LPR));
-    int64_t k0 = 0, k1 = 0;
-    if (IMPL != 0 && gid < d) {
-        k0 = __ldg(rowptr + gid);
-        k1 = __ldg(rowptr + gid + 1);
-    }
-    for (int64_t row = gid; row < d; row += ngroups) {
-        float4 acc;
-        if (IMPL == 0) {
-            k0 = __ldg(rowptr + row);
-            k1 = __ldg(rowptr + row + 1);
-            acc = row_product<MP, GATHER, IMPL>(k0, k1, col, val, args.x, vbits, lig, p0, wsel, bsh, mask, gmask);
-        } else {
-            // row pointers of this group's next row, loaded ahead
-            int64_t n0 = 0, n1 = 0;
-            if (row + ngroups < d) {
-                n0 = __ldg(rowptr + row + ngroups);
-                n1 = __ldg(rowptr + row + ngroups + 1);
-            }
-            acc = row_product<MP, GATHER, IMPL>(k0, k1, col, val, args.x, vbits, lig, p0, wsel, bsh, mask, gmask);
-            k0 = n0;
-            k1 = n1;
-        }
+    auto finish = [&](int64_t row, const float4& acc, const RowOperands& o) {
         float4 res;
         if (EPI == 0) {
             res = acc;
         } else {
-            const float4 v = signs4(__ldg(vbits + row * NW + wsel), bsh, mask);
-            const float4 own = (PREV == 0) ? v : ldg4(args.own + row * MP + p0);
-            const float4 pv = (PREV == 2) ? ldcs4(args.wprev + row * MP + p0) : v;
-            res = recurrence_update<PREV>(acc, own, pv, scale, scale_lo, shift, shift_lo);
-            tacc.x = fmaf(v.x, res.x, tacc.x);
-            tacc.y = fmaf(v.y, res.y, tacc.y);
-            tacc.z = fmaf(v.z, res.z, tacc.z);
-            tacc.w = fmaf(v.w, res.w, tacc.w);
+            res = recurrence_update<PREV>(acc, o.own, o.pv, scale, scale_lo, shift, shift_lo);
+            tacc.x = fmaf(o.v.x, res.x, tacc.x);
+            tacc.y = fmaf(o.v.y, res.y, tacc.y);
+            tacc.z = fmaf(o.v.z, res.z, tacc.z);
+            tacc.w = fmaf(o.v.w, res.w, tacc.w);
         }
         st4(args.out + row * MP + p0, res);
-    }
+    };
+    extern __shared__ float4 ring[];
+    rows_all<MP, GATHER, PREV, EPI, IMPL>(args, val, gid, args.d, ngroups, lig, p0, wsel, bsh, mask, gmask, ring,
+                                          finish);
 
     if (EPI == 1) {
         __shared__ double red[WPB][MP];
@@ -269,18 +529,27 @@ __global__ void __launch_bounds__(kThreads, StepOccupancy<IMPL>::value) step_ker
     }
 }
 
+template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
+cudaError_t launch_one_step(int grid, cudaStream_t s, const StepArgs& a) {
+    constexpr auto kern = step_kernel<MP, VT, GATHER, PREV, EPI, IMPL>;
+    constexpr int smem = step_smem<IMPL, GATHER>();
+    cudaError_t e = smem_opt_in<kern>(smem);
+    if (e != cudaSuccess || grid == 0) return e;  // grid 0: opt in only
+    kern<<<grid, kThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int MP, typename VT, int IMPL>
 cudaError_t launch_step_impl(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
     switch (kind) {
-        case kStepFirst: step_kernel<MP, VT, 1, 0, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepSecond: step_kernel<MP, VT, 0, 1, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepGeneral: step_kernel<MP, VT, 0, 2, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kProdBits: step_kernel<MP, VT, 1, 0, 0, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kProdFloat: step_kernel<MP, VT, 0, 0, 0, IMPL><<<grid, kThreads, 0, s>>>(a); break;
-        case kStepFirstFromFloat: step_kernel<MP, VT, 0, 0, 1, IMPL><<<grid, kThreads, 0, s>>>(a); break;
+        case kStepFirst: return launch_one_step<MP, VT, 1, 0, 1, IMPL>(grid, s, a);
+        case kStepSecond: return launch_one_step<MP, VT, 0, 1, 1, IMPL>(grid, s, a);
+        case kStepGeneral: return launch_one_step<MP, VT, 0, 2, 1, IMPL>(grid, s, a);
+        case kProdBits: return launch_one_step<MP, VT, 1, 0, 0, IMPL>(grid, s, a);
+        case kProdFloat: return launch_one_step<MP, VT, 0, 0, 0, IMPL>(grid, s, a);
+        case kStepFirstFromFloat: return launch_one_step<MP, VT, 0, 0, 1, IMPL>(grid, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <int MP, typename VT>
@@ -289,6 +558,8 @@ cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepAr
         case 0: return launch_step_impl<MP, VT, 0>(kind, grid, s, a);
         case 1: return launch_step_impl<MP, VT, 1>(kind, grid, s, a);
         case 2: return launch_step_impl<MP, VT, 2>(kind, grid, s, a);
+        case 3: return launch_step_impl<MP, VT, 3>(kind, grid, s, a);
+        case 4: return launch_step_impl<MP, VT, 4>(kind, grid, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -306,16 +577,26 @@ cudaError_t launch_step_vt(int panel, StepKind kind, int grid, cudaStream_t s, c
     }
 }
 
+template <int MP, typename VT, int IMPL>
+int ctas_per_sm_impl() {
+    constexpr auto kern = step_kernel<MP, VT, 0, 2, 1, IMPL>;
+    constexpr int smem = step_smem<IMPL, 0>();
+    int n = 0;
+    if (smem_opt_in<kern>(smem) != cudaSuccess) return 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 1;
+    return n > 0 ? n : 1;
+}
+
 template <int MP, typename VT>
 int ctas_per_sm_mp(int impl) {
-    int n = 0;
-    cudaError_t e = impl == 0
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1, 0>, kThreads, 0)
-        : impl == 1
-        ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1, 1>, kThreads, 0)
-        : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, step_kernel<MP, VT, 0, 2, 1, 2>, kThreads, 0);
-    if (e != cudaSuccess) return 1;
-    return n > 0 ? n : 1;
+    switch (impl) {
+        case 0: return ctas_per_sm_impl<MP, VT, 0>();
+        case 1: return ctas_per_sm_impl<MP, VT, 1>();
+        case 2: return ctas_per_sm_impl<MP, VT, 2>();
+        case 3: return ctas_per_sm_impl<MP, VT, 3>();
+        case 4: return ctas_per_sm_impl<MP, VT, 4>();
+        default: return 1;
+    }
 }
 
 template <typename VT>

@@ -44,6 +44,26 @@ def test_general_matches_oracle(torch, d, M, n):
     m.close()
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+def test_general_kernel_variants(torch, variant):
+    """Algorithm 2's two products per step (C x, then C^T y with the recurrence)
+    with every inner-loop variant, including the ring's plain-product form."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    d, M, n = 1500, 32, 20
+    C = workloads.nonsymmetric_dominant(d, 3, 11)
+    c32, c64 = C.stored("f32")
+    a, b = gen_interval(workloads.Csr(C.rowptr, C.col, c64))
+    m = CsrLogdet(C.rowptr, C.col, c32, kind="general")
+    m.set_kernel_variant(variant)
+    m.set_interval(a, b)
+    r = m.estimate(n, M, 5, moments=True)
+    m.close()
+    ref = oracle.estimate(C.rowptr, C.col, c64, a, b, n, M, seed=5, kind=1)
+    assert np.all(np.abs(r["t"] - ref["t"]) <= moment_tol(d, n))
+    assert abs(r["logdet"] - ref["gamma"] / 2) <= 1e-5 * abs(ref["gamma"] / 2)
+
+
 def test_general_vs_exact_with_high_degree(torch):
     """Against numpy's log|det C|: statistical (M = 256) within 5 stderr."""
     from paper_1503_06394_gb300 import CsrLogdet

@@ -55,7 +55,7 @@ def test_parity_shapes(torch, d, M):
     check(B, "f32", 12, M, seed=d + M)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("M", [3, 8, 16, 32, 64, 128])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_parity_kernel_variants(torch, variant, M, dtype):
@@ -79,6 +79,39 @@ def test_parity_kernel_variants(torch, variant, M, dtype):
     S = workloads._with_diagonal(d, sym, rs + 1.0, "sym")
     S.val = S.val / (2 * rs.max() + 1.0)
     check(S, dtype, 9, M, seed=M + variant, variant=variant)
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+@pytest.mark.parametrize("M", [16, 64])
+def test_parity_ring_variants_grid(torch, variant, M):
+    """The shared-memory ring variants on a 64 x 64 five-point grid (every row
+    inside the staged chunk, neighbour rows shared between groups) against the
+    oracle."""
+    B = workloads.grid_gmrf(64, 0.1)
+    check(B, "f32", 20, M, seed=M + variant, interval=(0.1, 8.1), structured=True, variant=variant)
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_ring_variants_first_use_in_graph(torch, variant):
+    """FP64 values with a ring variant are used by no other test, so their
+    kernels meet the shared-memory opt-in first on the way into a CUDA graph
+    capture; the replays equal the plain launches and the oracle."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    B = workloads.sparse_random_spd(3000, 3, 77)
+    _, v64 = B.stored("f64")
+    a, b = oracle.gershgorin(B.rowptr, B.col, v64)
+    m = CsrLogdet(B.rowptr, B.col, v64, dtype="f64")
+    m.set_kernel_variant(variant)
+    m.set_interval(a, b)
+    m.set_graph(True)
+    graph = [m.estimate(15, 24, s)["logdet"] for s in (0, 1, 0)]
+    m.set_graph(False)
+    plain = [m.estimate(15, 24, s)["logdet"] for s in (0, 1)]
+    m.close()
+    assert graph == [plain[0], plain[1], plain[0]]
+    ref = oracle.estimate(B.rowptr, B.col, v64, a, b, 15, 24, seed=1)
+    assert abs(plain[1] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
 
 
 @pytest.mark.parametrize("n", [0, 1, 2, 3])
@@ -272,7 +305,7 @@ def test_autotune_keeps_parity(torch):
     m = CsrLogdet(B.rowptr, B.col, v32)
     m.set_interval(lo, hi)
     variant, ms = m.autotune(20, 32)
-    assert variant in (0, 1, 2) and ms > 0
+    assert variant in (0, 1, 2, 3, 4) and ms > 0
     r = m.estimate(20, 32, 1)
     ref = oracle.estimate(B.rowptr, B.col, v64, lo, hi, 20, 32, seed=1)
     assert abs(r["logdet"] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
