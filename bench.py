@@ -62,9 +62,9 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index=0):
+    def __init__(self, gpu_index=0, name="clocks_bench.csv"):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        self.path = os.path.join(ROOT, "gpurun_out", name)
         self.gpu_index = gpu_index
 
     def __enter__(self):
@@ -90,7 +90,7 @@ class ClockSampler:
     def summary(self):
         if self.proc is None or not os.path.exists(self.path):
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        sm, smax, reasons = [], [], set()
+        sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [x.strip() for x in line.split(",")]
@@ -101,13 +101,17 @@ class ClockSampler:
                 smax.append(float(parts[2]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(parts[3]))
+            except ValueError:
+                pass
             for nm, v in zip(names, parts[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "samples": len(sm),
-                "reasons": sorted(reasons)}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "sm_min_mhz": float(min(sm)),
+                "power_w": float(np.median(pw)) if pw else None, "samples": len(sm), "reasons": sorted(reasons)}
 
 
 def build_workload(cfg_id, d_override=None):
@@ -285,6 +289,26 @@ def run_ours(args, rank, world):
     del m
     torch.cuda.empty_cache()
 
+    # end to end through the host-buffer entry point (pinned host arrays), right
+    # after the device-timed region and under the same conditions
+    rp = torch.from_numpy(B.rowptr).pin_memory()
+    cl = torch.from_numpy(B.col).pin_memory()
+    vv = torch.from_numpy(stored.view(np.int16) if args.dtype == "bf16" else stored).pin_memory()
+    need = Bd.cld_host_workspace_size(B.d, B.nnz, {"f32": 0, "bf16": 1, "f64": 2}[args.dtype], n, M)
+    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
+    logdet_host(rp, cl, vv, a_e, b_e, n, M, seed, dtype=args.dtype, workspace=ws)
+    torch.cuda.synchronize()
+    e2e_t = []
+    with ClockSampler(local, "clocks_e2e.csv") as clk_e2e:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            logdet_host(rp, cl, vv, a_e, b_e, n, M, seed, dtype=args.dtype, workspace=ws)
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_s = float(np.mean(e2e_t))
+    h2d = (B.d + 1) * 8 + B.nnz * 4 + B.nnz * s_v
+    del ws
+    torch.cuda.empty_cache()
+
     # BF16-stored values on the same GPU (FP32 recurrence vectors)
     bf16 = None
     if args.dtype == "f32" and not args.no_bf16:
@@ -319,24 +343,6 @@ def run_ours(args, rank, world):
     if not args.no_latency and args.d is None:
         latency = latency_leg(args, torch)
 
-    # end to end through the host-buffer entry point (pinned host arrays)
-    rp = torch.from_numpy(B.rowptr).pin_memory()
-    cl = torch.from_numpy(B.col).pin_memory()
-    vv = torch.from_numpy(stored.view(np.int16) if args.dtype == "bf16" else stored).pin_memory()
-    need = Bd.cld_host_workspace_size(B.d, B.nnz, {"f32": 0, "bf16": 1, "f64": 2}[args.dtype], n, M)
-    ws = torch.empty(need, dtype=torch.uint8, device="cuda")
-    logdet_host(rp, cl, vv, a_e, b_e, n, M, seed, dtype=args.dtype, workspace=ws)
-    torch.cuda.synchronize()
-    e2e_t = []
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        logdet_host(rp, cl, vv, a_e, b_e, n, M, seed, dtype=args.dtype, workspace=ws)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e_t))
-    h2d = (B.d + 1) * 8 + B.nnz * 4 + B.nnz * s_v
-    del ws
-    torch.cuda.empty_cache()
-
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -360,7 +366,8 @@ def run_ours(args, rank, world):
                          "avg_launch_ms": kernel_avg_ms, "peak_source": peak_src},
             "gpu_launches": total_launches,
             "e2e": {"value": world * n * bstep / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": 32, "seconds_per_step": e2e_s},
+                    "d2h_bytes_per_step": 32, "seconds_per_step": e2e_s,
+                    "seconds_each": [round(t, 5) for t in e2e_t], "clocks": clk_e2e.summary()},
             "clocks": clk.summary(), "generation_s": gen_s}
     if bf16 is not None:
         line["bf16"] = bf16

@@ -154,8 +154,8 @@ __device__ __forceinline__ float4 tail_product(float4 acc, int64_t k0, int64_t k
 // IMPL 1 (2): the LPR lanes of the group load the next 8 (4) (index, value) pairs
 //         cooperatively (one coalesced access per lane) and chunk_product
 //         consumes them.
-// IMPL 3 and 4 (the shared-memory ring) do not go through row_product for
-// float gathers; see rows_ring.
+// IMPL 3 and 4 (the shared-memory ring) do not go through row_product; see
+// rows_ring.
 //
 // The shuffles of the cooperative variants name only the LPR lanes of the
 // row's group (gmask): groups of one warp own rows of different lengths, so
@@ -268,8 +268,9 @@ __device__ __forceinline__ void rows_plain(const StepArgs& args, const VT* __res
 // holding loads in flight in registers, so a group keeps the next row's
 // gathers in flight while it consumes the current one without the register
 // cost that would lower occupancy.  Per group and row: the first RC stored
-// entries' rows of w_j, w_j's own row and w_{j-1}'s row go to one of two
-// stages; entries past RC are gathered directly (tail_product, same order).
+// entries' rows of w_j (or, for sign gathers, the 4-byte sign word of each),
+// w_j's own row and w_{j-1}'s row go to one of two stages; entries past RC are
+// gathered directly (tail_product, same order).
 template <int IMPL>
 struct RingChunk { static constexpr int value = IMPL == 3 ? 5 : 8; };
 
@@ -282,6 +283,10 @@ __host__ __device__ constexpr int ring_bytes(int impl) {
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -297,7 +302,7 @@ __device__ __forceinline__ void cp_async_wait() {
 // flight), and consumes r.  Each thread reads only the slots it copied, so
 // its own cp.async.wait_group orders them; a slot is rewritten only by the
 // same thread after its value was consumed (in-order issue).
-template <int MP, int PREV, int EPI, int RC, typename VT, class Finish>
+template <int MP, int GATHER, int PREV, int EPI, int RC, typename VT, class Finish>
 __device__ __forceinline__ void rows_ring(const StepArgs& args, const VT* __restrict__ val, int64_t first,
                                           int64_t end, int64_t stride, int lig, int p0, int wsel, int bsh,
                                           float4 mask, unsigned gmask, float4* ring, Finish&& finish) {
@@ -313,7 +318,12 @@ __device__ __forceinline__ void rows_ring(const StepArgs& args, const VT* __rest
 #pragma unroll
         for (int q = 0; q < RC; ++q) {
             const int c = __shfl_sync(gmask, cr[q / LPR], q % LPR, LPR);
-            if (k0 + q < k1) cp_async16(slot(st, q), args.x + (int64_t)c * MP + p0);
+            if (k0 + q < k1) {
+                if (GATHER == 1)
+                    cp_async4(slot(st, q), args.vbits + (int64_t)c * NW + wsel);
+                else
+                    cp_async16(slot(st, q), args.x + (int64_t)c * MP + p0);
+            }
         }
         if (kOwn) cp_async16(slot(st, RC), args.own + row * MP + p0);
         if (kPrev) cp_async16(slot(st, RC + 1), args.wprev + row * MP + p0);
@@ -373,7 +383,8 @@ __device__ __forceinline__ void rows_ring(const StepArgs& args, const VT* __rest
         for (int q = 0; q < RC; ++q) {
             const float av = __shfl_sync(gmask, vr[q / LPR], q % LPR, LPR);
             if (k0 + q < k1) {
-                const float4 xv = *slot(st, q);
+                const float4 xv = GATHER == 1 ? signs4(*reinterpret_cast<const uint32_t*>(slot(st, q)), bsh, mask)
+                                              : *slot(st, q);
                 acc.x = fmaf(av, xv.x, acc.x);
                 acc.y = fmaf(av, xv.y, acc.y);
                 acc.z = fmaf(av, xv.z, acc.z);
@@ -381,7 +392,7 @@ __device__ __forceinline__ void rows_ring(const StepArgs& args, const VT* __rest
             }
         }
         if (k0 + RC < k1)
-            acc = tail_product<MP, 0>(acc, k0 + RC, k1, args.col, val, args.x, args.vbits, p0, wsel, bsh, mask);
+            acc = tail_product<MP, GATHER>(acc, k0 + RC, k1, args.col, val, args.x, args.vbits, p0, wsel, bsh, mask);
         RowOperands o;
         if (EPI == 0) {
             o.v = o.own = o.pv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -409,32 +420,29 @@ __device__ __forceinline__ void rows_ring(const StepArgs& args, const VT* __rest
     cp_async_wait<0>();
 }
 
-// The row loop of variant IMPL; sign gathers (GATHER 1) of the ring variants
-// take variant 0's loop.
+// The row loop of variant IMPL.
 template <int MP, int GATHER, int PREV, int EPI, int IMPL, typename VT, class Finish>
 __device__ __forceinline__ void rows_all(const StepArgs& args, const VT* __restrict__ val, int64_t first,
                                          int64_t end, int64_t stride, int lig, int p0, int wsel, int bsh,
                                          float4 mask, unsigned gmask, float4* ring, Finish&& finish) {
-    if constexpr (IMPL >= 3 && GATHER == 0)
-        rows_ring<MP, PREV, EPI, RingChunk<IMPL>::value>(args, val, first, end, stride, lig, p0, wsel, bsh, mask,
-                                                         gmask, ring, finish);
+    if constexpr (IMPL >= 3)
+        rows_ring<MP, GATHER, PREV, EPI, RingChunk<IMPL>::value>(args, val, first, end, stride, lig, p0, wsel, bsh,
+                                                                 mask, gmask, ring, finish);
     else
-        rows_plain<MP, GATHER, PREV, EPI, (IMPL >= 3 ? 0 : IMPL)>(args, val, first, end, stride, lig, p0, wsel, bsh,
-                                                                  mask, gmask, finish);
+        rows_plain<MP, GATHER, PREV, EPI, IMPL>(args, val, first, end, stride, lig, p0, wsel, bsh, mask, gmask,
+                                                finish);
 }
 
 // Resident-CTA targets per variant (256 threads): 6 (40 registers), 3, 4;
 // the ring variants are bounded by their shared memory (3 and 2 CTAs).
-// Sign gathers (GATHER 1) of the ring variants run variant 0's loop and target.
 template <int IMPL, int GATHER = 0>
 struct StepOccupancy {
-    static constexpr int I = (IMPL >= 3 && GATHER == 1) ? 0 : IMPL;
-    static constexpr int value = I == 0 ? 6 : I == 1 ? 3 : I == 2 ? 4 : I == 3 ? 3 : 2;
+    static constexpr int value = IMPL == 0 ? 6 : IMPL == 1 ? 3 : IMPL == 2 ? 4 : IMPL == 3 ? 3 : 2;
 };
 
 // Dynamic shared memory of one instantiation.
 template <int IMPL, int GATHER>
-constexpr int step_smem() { return (IMPL >= 3 && GATHER == 0) ? ring_bytes(IMPL) : 0; }
+constexpr int step_smem() { return ring_bytes(IMPL); }
 
 // Opts kernel K into `bytes` of dynamic shared memory on the current device,
 // once per device (the attribute is per device; ordinals >= 64 set it on
