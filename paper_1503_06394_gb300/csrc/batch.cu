@@ -17,6 +17,8 @@ namespace cld {
 template <int MP, typename VT, int GATHER, int PREV, int IMPL>
 __global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value))
     batch_step_kernel(const BatchStepArgs ba) {
+    pdl_wait();  // w_j, w_{j-1}, the signs, tiles and parameters come from earlier kernels
+    pdl_trigger();
     constexpr int LPR = MP / 4;
     constexpr int GPW = 32 / LPR;
     constexpr int WPB = kThreads / 32;
@@ -81,8 +83,7 @@ static cudaError_t launch_one_batch(int grid, cudaStream_t s, const BatchStepArg
     constexpr int smem = step_smem<IMPL, GATHER>();
     cudaError_t e = smem_opt_in<kern>(smem);
     if (e != cudaSuccess || grid == 0) return e;  // grid 0: opt in only
-    kern<<<grid, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, smem, s, a);
 }
 
 template <int MP, typename VT, int IMPL>

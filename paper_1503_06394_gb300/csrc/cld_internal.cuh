@@ -82,6 +82,17 @@ __device__ __forceinline__ float4 signs4(uint32_t word, int sh, float4 mask) {
     return s;
 }
 
+// ------------------------------------------------------------------ PDL
+// Programmatic dependent launch: a kernel launched with the programmatic
+// stream-serialization attribute may become resident before its predecessor
+// in the stream has finished.  pdl_wait() returns once the predecessor grid
+// has completed and its memory writes are visible (at once when there is no
+// programmatic predecessor); pdl_trigger() lets this kernel's own successor be
+// scheduled.  Every read of data written by earlier kernels follows
+// pdl_wait().
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ values
 struct bf16_t { uint16_t bits; };
 

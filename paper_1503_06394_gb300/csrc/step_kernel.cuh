@@ -444,6 +444,24 @@ struct StepOccupancy {
 template <int IMPL, int GATHER>
 constexpr int step_smem() { return ring_bytes(IMPL); }
 
+// Launches kern<<<grid, kThreads, smem, s>>>(arg) with programmatic stream
+// serialization (see pdl_wait): consecutive step launches overlap their
+// launch latency with the predecessor's tail, in streams and in graphs.
+template <typename Arg>
+cudaError_t launch_pdl(void (*kern)(Arg), int grid, int smem, cudaStream_t s, const Arg& arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 // Opts kernel K into `bytes` of dynamic shared memory on the current device,
 // once per device (the attribute is per device; ordinals >= 64 set it on
 // every call).  Needed above 48 KB, before the first launch or occupancy query.
@@ -466,6 +484,8 @@ __global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value)
 
 template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
 __global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value)) step_kernel(const StepArgs args) {
+    pdl_wait();  // w_j, w_{j-1}, the signs and the parameters come from earlier kernels
+    pdl_trigger();
     constexpr int LPR = MP / 4;          // lanes per row
     constexpr int GPW = 32 / LPR;        // rows per warp
     constexpr int WPB = kThreads / 32;
@@ -543,8 +563,7 @@ cudaError_t launch_one_step(int grid, cudaStream_t s, const StepArgs& a) {
     constexpr int smem = step_smem<IMPL, GATHER>();
     cudaError_t e = smem_opt_in<kern>(smem);
     if (e != cudaSuccess || grid == 0) return e;  // grid 0: opt in only
-    kern<<<grid, kThreads, smem, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(kern, grid, smem, s, a);
 }
 
 template <int MP, typename VT, int IMPL>
