@@ -482,6 +482,7 @@ def batch_leg(args, torch):
             bt = CsrBatchLogdet(br, S.rowptr, S.col, st, dtype=dtype, kind=kind)
             bt.auto_intervals()
             v, _ = bt.autotune(n, M)
+            tile_rows = bt.tile_rows
             bt.set_graph(True)
             bt.reserve(n, M)
             for _ in range(2):
@@ -500,6 +501,7 @@ def batch_leg(args, torch):
             out["%s_%s_ms" % (kind, dtype)] = ms
             out["%s_%s_gbs" % (kind, dtype)] = nbytes / (ms / 1e3) / 1e9
             out["%s_%s_variant" % (kind, dtype)] = v
+            out["%s_%s_tile_rows" % (kind, dtype)] = tile_rows
             tot_ms += ms
             tot_bytes += nbytes
         out["batched_%s_ms" % dtype] = tot_ms

@@ -227,8 +227,12 @@ CLD_API cld_status cld_create_batch(cld_handle* out, int nb, const int64_t* blk_
                                     cld_dtype val_dtype, cld_kind kind, void* stream);
 
 /* Rows per work tile of the batched step kernel (>= 256; default 1024): a
- * tile never spans two blocks; CTAs take tiles from a static queue. */
+ * tile never spans two blocks; CTAs take tiles from a static queue.
+ * cld_autotune on a batch handle also picks it (256 ... 4096). */
 CLD_API cld_status cld_batch_set_tile_rows(cld_handle h, int rows);
+
+/* The current rows per tile of a batch handle.  Errors: CLD_ERR_INVALID. */
+CLD_API cld_status cld_batch_get_tile_rows(cld_handle h, int* rows);
 
 /* Per-block intervals (host arrays of nb doubles), as cld_set_interval. */
 CLD_API cld_status cld_batch_set_intervals(cld_handle h, const double* a, const double* b);
@@ -271,7 +275,10 @@ CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
 /* Autotuner: times `reps` launches of the general recurrence step of every
  * variant on this matrix with M probes (workspace and interval must be set;
  * the workspace contents are overwritten) and keeps the fastest on the handle
- * (the current variant stays unless another is at least 2 % faster).
+ * (the current choice stays unless another is at least 2 % faster).  On a
+ * batch handle every variant is timed at every tile size of 256, 512, 1024,
+ * 2048 and 4096 rows and the fastest pair is kept (read the tile size back
+ * with cld_batch_get_tile_rows).
  * Returns the chosen variant and its mean step time in ms (either may be NULL).
  * Errors: CLD_ERR_INVALID, CLD_ERR_NOMEM, CLD_ERR_INTERVAL, CLD_ERR_CUDA. */
 CLD_API cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* ms_out);

@@ -43,6 +43,7 @@ SIGNATURES = [
                                    _P(_f64), _P(_f64)]),
     ("cld_create_batch", _i32, [_P(_vp), _i32, _vp, _i64, _vp, _vp, _vp, _i32, _i32, _vp]),
     ("cld_batch_set_tile_rows", _i32, [_vp, _i32]),
+    ("cld_batch_get_tile_rows", _i32, [_vp, _P(_i32)]),
     ("cld_batch_set_intervals", _i32, [_vp, _vp, _vp]),
     ("cld_batch_auto_intervals", _i32, [_vp, _vp, _vp]),
     ("cld_batch_estimate", _i32, [_vp, _i32, _i32, _u64, _vp, _vp]),
@@ -195,6 +196,12 @@ def cld_create_batch(blk_rows, nnz, rowptr, col, val, val_dtype, kind, stream=0)
     _check(load().cld_create_batch(ctypes.byref(h), br.shape[0] - 1, _ptr(br), nnz, _ptr(rowptr), _ptr(col),
                                    _ptr(val), val_dtype, kind, stream or None))
     return h.value
+
+
+def cld_batch_get_tile_rows(h):
+    r = ctypes.c_int32()
+    _check(load().cld_batch_get_tile_rows(h, ctypes.byref(r)))
+    return r.value
 
 
 def cld_batch_set_tile_rows(h, rows):

@@ -201,6 +201,11 @@ class CsrBatchLogdet(CsrLogdet):
     def set_tile_rows(self, rows: int):
         B.cld_batch_set_tile_rows(self.h, rows)
 
+    @property
+    def tile_rows(self) -> int:
+        """Rows per work tile (chosen by autotune(), or set_tile_rows())."""
+        return B.cld_batch_get_tile_rows(self.h)
+
     def estimate(self, n: int, M: int, seed: int = 0):
         self.reserve(n, M)
         g, se = B.cld_batch_estimate(self.h, self.nb, n, M, seed)

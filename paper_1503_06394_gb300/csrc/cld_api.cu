@@ -985,6 +985,14 @@ cld_status cld_create_batch(cld_handle* out, int nb, const int64_t* blk_rows, in
     return CLD_OK;
 }
 
+cld_status cld_batch_get_tile_rows(cld_handle h, int* rows) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (h->nb == 0) return fail(CLD_ERR_INVALID, "not a batch handle");
+    if (!rows) return fail(CLD_ERR_INVALID, "rows is NULL");
+    *rows = h->tile_rows;
+    return CLD_OK;
+}
+
 cld_status cld_batch_set_tile_rows(cld_handle h, int rows) {
     if (check_handle(h)) return CLD_ERR_INVALID;
     if (h->nb == 0) return fail(CLD_ERR_INVALID, "not a batch handle");
@@ -1103,70 +1111,98 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     if (h->d == 0) return fail(CLD_ERR_INVALID, "empty matrix");
     if (h->dense) return fail(CLD_ERR_UNSUPPORTED, "the dense path has a single kernel");
     const int saved = h->impl;
-    int best = -1;
+    const int saved_tiles = h->tile_rows;
+    int best = -1, best_tiles = saved_tiles;
     float best_ms = 0.f, saved_ms = -1.f;
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    for (int v = 0; v < kNumStepImpls; ++v) {
-        h->impl = v;
-        const Layout L = make_layout(h, 2, M, 0);
-        if (L.total > h->ws_bytes) continue;
-        // Timing runs of the general step on the current workspace contents
-        // (whatever they hold: the cost does not depend on the values).
-        StepArgs a{};
-        a.d = h->d;
-        a.vbits = at<uint32_t>(h, L.vbits);
-        a.prm = at<Params>(h, L.params);
-        a.mreal = M < L.panel ? M : L.panel;
-        a.impl = v;
-        const bool general = h->kind == CLD_GENERAL;
-        a.rowptr = general ? at<int64_t>(h, L.rowptrT) : h->rowptr;
-        a.col = general ? at<int32_t>(h, L.colT) : h->col;
-        a.val = general ? at<void>(h, L.valT) : h->val;
-        a.x = at<float>(h, L.W[1]);
-        a.own = at<float>(h, L.W[1]);
-        a.wprev = at<float>(h, L.W[0]);
-        a.out = at<float>(h, L.W[2]);
-        a.tpart = at<double>(h, L.tpart);
-        CUDA_TRY(cudaMemsetAsync(at<float>(h, L.W[0]), 0, 3 * ((size_t)h->d * L.panel * 4), h->stream));
-        BatchStepArgs ba{};
-        int bgrid = L.grid;
-        if (h->nb > 0) {  // batches: time the tile-queue kernel
-            ba.s = a;
-            ba.tiles = at<Tile>(h, L.tiles);
-            ba.ntiles = (int64_t)h->tiles.size();
-            ba.bprm = at<Params>(h, L.bprm);
-            ba.tpart = at<double>(h, L.tpart);
-            bgrid = (int)(ba.ntiles < L.grid ? (ba.ntiles > 0 ? ba.ntiles : 1) : L.grid);
+    // batches: every variant at every tile size; single matrices: variants only
+    static const int kTileRows[] = {256, 512, 1024, 2048, 4096};
+    const int ntiles_cand = h->nb > 0 ? (int)(sizeof(kTileRows) / sizeof(kTileRows[0])) : 1;
+    for (int ti = 0; ti < ntiles_cand; ++ti) {
+        if (h->nb > 0) {
+            h->tile_rows = kTileRows[ti];
+            build_tiles(h);
+            const cld_status ust = upload_batch_tables(h, make_layout(h, 0, 1, 0));
+            if (ust != CLD_OK) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return ust;
+            }
         }
-        auto one = [&]() {
-            return h->nb > 0 ? launch_batch_step(L.panel, (int)h->dtype, kStepGeneral, bgrid, h->stream, ba)
-                             : launch_step(L.panel, (int)h->dtype, kStepGeneral, L.grid, h->stream, a);
-        };
-        CUDA_TRY(one());  // warm-up
-        CUDA_TRY(cudaEventRecord(e0, h->stream));
-        for (int r = 0; r < reps; ++r) CUDA_TRY(one());
-        CUDA_TRY(cudaEventRecord(e1, h->stream));
-        CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        ms /= reps;
-        if (v == saved) saved_ms = ms;
-        if (best < 0 || ms < best_ms) { best = v; best_ms = ms; }
+        for (int v = 0; v < kNumStepImpls; ++v) {
+            h->impl = v;
+            const Layout L = make_layout(h, 2, M, 0);
+            if (L.total > h->ws_bytes) continue;
+            // Timing runs of the general step on the current workspace contents
+            // (whatever they hold: the cost does not depend on the values).
+            StepArgs a{};
+            a.d = h->d;
+            a.vbits = at<uint32_t>(h, L.vbits);
+            a.prm = at<Params>(h, L.params);
+            a.mreal = M < L.panel ? M : L.panel;
+            a.impl = v;
+            const bool general = h->kind == CLD_GENERAL;
+            a.rowptr = general ? at<int64_t>(h, L.rowptrT) : h->rowptr;
+            a.col = general ? at<int32_t>(h, L.colT) : h->col;
+            a.val = general ? at<void>(h, L.valT) : h->val;
+            a.x = at<float>(h, L.W[1]);
+            a.own = at<float>(h, L.W[1]);
+            a.wprev = at<float>(h, L.W[0]);
+            a.out = at<float>(h, L.W[2]);
+            a.tpart = at<double>(h, L.tpart);
+            CUDA_TRY(cudaMemsetAsync(at<float>(h, L.W[0]), 0, 3 * ((size_t)h->d * L.panel * 4), h->stream));
+            BatchStepArgs ba{};
+            int bgrid = L.grid;
+            if (h->nb > 0) {  // batches: time the tile-queue kernel
+                ba.s = a;
+                ba.tiles = at<Tile>(h, L.tiles);
+                ba.ntiles = (int64_t)h->tiles.size();
+                ba.bprm = at<Params>(h, L.bprm);
+                ba.tpart = at<double>(h, L.tpart);
+                bgrid = (int)(ba.ntiles < L.grid ? (ba.ntiles > 0 ? ba.ntiles : 1) : L.grid);
+            }
+            auto one = [&]() {
+                return h->nb > 0 ? launch_batch_step(L.panel, (int)h->dtype, kStepGeneral, bgrid, h->stream, ba)
+                                 : launch_step(L.panel, (int)h->dtype, kStepGeneral, L.grid, h->stream, a);
+            };
+            CUDA_TRY(one());  // warm-up
+            CUDA_TRY(cudaEventRecord(e0, h->stream));
+            for (int r = 0; r < reps; ++r) CUDA_TRY(one());
+            CUDA_TRY(cudaEventRecord(e1, h->stream));
+            CUDA_TRY(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+            ms /= reps;
+            if (v == saved && h->tile_rows == saved_tiles) saved_ms = ms;
+            if (best < 0 || ms < best_ms) {
+                best = v;
+                best_ms = ms;
+                best_tiles = h->tile_rows;
+            }
+        }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (best < 0) {
         h->impl = saved;
-        return fail(CLD_ERR_NOMEM, "workspace too small to time any variant");
+        best_tiles = saved_tiles;
     }
-    // keep the current variant unless another is at least 2 % faster, so that
-    // timing noise does not flip the choice (and the summation order) run to run
-    if (saved_ms > 0.f && saved_ms <= 1.02f * best_ms) {
+    // keep the current choice unless another is at least 2 % faster, so that
+    // timing noise does not flip it (and the summation order) run to run
+    if (best >= 0 && saved_ms > 0.f && saved_ms <= 1.02f * best_ms) {
         best = saved;
         best_ms = saved_ms;
+        best_tiles = saved_tiles;
     }
+    if (h->nb > 0 && h->tile_rows != best_tiles) {
+        h->tile_rows = best_tiles;
+        build_tiles(h);
+        const cld_status ust = upload_batch_tables(h, make_layout(h, 0, 1, 0));
+        if (ust != CLD_OK) return ust;
+    }
+    if (best < 0) return fail(CLD_ERR_NOMEM, "workspace too small to time any variant");
     h->impl = best;
     if (variant_out) *variant_out = best;
     if (ms_out) *ms_out = best_ms;

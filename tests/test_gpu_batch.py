@@ -150,6 +150,29 @@ def test_batch_tile_rows(torch):
         np.testing.assert_allclose(r, res[0], rtol=1e-6)  # FP32 per-thread sums follow the tiling
 
 
+def test_batch_autotune_picks_tiles(torch):
+    """The batch autotuner times every variant at tile sizes 256 ... 4096, keeps
+    a (variant, tile size) pair, leaves that tile size installed, and the
+    estimate after it still matches the oracle block by block."""
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = spd_mats([3000, 900, 5000, 257], 23)
+    br, S = workloads.block_diag(mats)
+    s32, s64 = S.stored("f32")
+    a, b = intervals(mats)
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    bt.set_intervals(a, b)
+    v, ms = bt.autotune(20, 32)
+    assert v in range(5) and ms > 0
+    assert bt.tile_rows in (256, 512, 1024, 2048, 4096)
+    got = bt.estimate(20, 32, 9)["logdet"]
+    bt.close()
+    for i, m in enumerate(mats):
+        _, m64 = m.stored("f32")
+        ref = oracle.estimate(m.rowptr, m.col, m64, a[i], b[i], 20, 32, seed=9 + i)
+        assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
+
+
 def test_batch_rejects_off_block_columns(torch):
     from paper_1503_06394_gb300 import CldError, CsrBatchLogdet
     from paper_1503_06394_gb300 import _binding as Bd
