@@ -418,11 +418,11 @@ def adjoint_leg(args, torch, world):
     m = CsrLogdet(K.rowptr, K.col, v32)
     m.set_interval(a, b)
     m.autotune(n, M)
-    m.reserve(n, M, 1)
+    ws_all = m.reserve(n, M, 1)
     m.estimate(n, M, 0)
     m.grad(n, M, 0)
     stream = torch.cuda.current_stream()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     steps = max(1, args.steps)
     torch.cuda.synchronize()
     e[0].record(stream)
@@ -435,14 +435,32 @@ def adjoint_leg(args, torch, world):
     torch.cuda.synchronize()
     fwd = e[0].elapsed_time(e[1]) / steps
     grd = e[1].elapsed_time(e[2]) / steps
+    # checkpointed reverse pass: pairs every K ~ sqrt(2n) steps, segments recomputed
+    kc = max(2, int(round((2 * n) ** 0.5)))
+    m.set_grad_checkpoint(kc)
+    m.ws = None
+    torch.cuda.empty_cache()
+    ws_ck = m.reserve(n, M, 1)
+    gc, Gc = m.grad(n, M, 0)
+    torch.cuda.synchronize()
+    e[2].record(stream)
+    for _ in range(steps):
+        gc, Gc = m.grad(n, M, 0)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    grd_ck = e[2].elapsed_time(e[3]) / steps
+    same = bool(gc == g and torch.equal(Gc, G))
     m.close()
-    del m, G
+    del m, G, Gc
     torch.cuda.empty_cache()
     return {"workload": "wendland npts=%d ell=%g sigma2=%g (nnz=%d, %.1f per row), n=%d, M=%d" % (
                 cfg["npts"], cfg["ell"], cfg["sigma2"], K.nnz, K.nnz / K.d, n, M),
             "interval": [a, b], "forward_ms": fwd, "grad_ms": grd,
             "adjoint_forward_ratio": grd / fwd, "reverse_over_forward": (grd - fwd) / fwd,
             "storage": "all w_j kept in HBM (%.1f GB)" % (n * K.d * 32 * 4 / 1e9),
+            "workspace_gb": ws_all / 1e9,
+            "checkpointed": {"interval": kc, "grad_ms": grd_ck, "adjoint_forward_ratio": grd_ck / fwd,
+                             "workspace_gb": ws_ck / 1e9, "bit_identical_to_store_all": same},
             "logdet": r["logdet"], "grad_logdet": g}
 
 

@@ -155,10 +155,21 @@ CLD_API cld_status cld_last_details(cld_handle h, double* coeffs_out, double* ga
  * FP32 device array of nnz entries, each stored entry treated as an
  * independent variable.  Reverse-mode differentiation of the recurrence of
  * Sec. 2.2 (an extension; the paper has no gradient).  CLD_SPD only.
- * Needs cld_workspace_size(h, n, M, 1).  Errors as cld_estimate, plus
- * CLD_ERR_UNSUPPORTED for CLD_GENERAL. */
+ * Needs cld_workspace_size(h, n, M, 1) (which follows the checkpoint
+ * interval below).  Errors as cld_estimate, plus CLD_ERR_UNSUPPORTED for
+ * CLD_GENERAL. */
 CLD_API cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
                     float* dvalues_dev);
+
+/* Memory of cld_grad.  interval 0 (default): the forward keeps every w_1..w_n
+ * (n blocks of d x panel floats).  interval K >= 2: the forward keeps only the
+ * pairs (w_{sK-1}, w_{sK}); the reverse pass recomputes w_{sK+1} .. w_{(s+1)K}
+ * from them, segment by segment from the last, before taking those reverse
+ * steps - about 2n/K + K blocks (K near sqrt(2n) is smallest) for one extra
+ * forward pass.  The gradient and the estimate are bit-identical to
+ * interval 0's (the recomputation repeats the same kernels on the same data).
+ * Errors: CLD_ERR_INVALID for 1, a negative value or more than 100000. */
+CLD_API cld_status cld_set_grad_checkpoint(cld_handle h, int interval);
 
 /* One-shot estimate from HOST arrays: copies the CSR (rowptr, col, val as
  * above but in host memory, ideally pinned) into the front of the device

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("cld_batch_estimate", _i32, [_vp, _i32, _i32, _u64, _vp, _vp]),
     ("cld_set_graph", _i32, [_vp, _i32]),
     ("cld_set_kernel_variant", _i32, [_vp, _i32]),
+    ("cld_set_grad_checkpoint", _i32, [_vp, _i32]),
     ("cld_autotune", _i32, [_vp, _i32, _i32, _P(_i32), _P(ctypes.c_float)]),
     ("cld_set_profiling", _i32, [_vp, _i32]),
     ("cld_last_timing", _i32, [_vp, _P(ctypes.c_float), _P(_i32), _P(_i32)]),
@@ -234,6 +235,10 @@ def cld_set_graph(h, on):
 
 def cld_set_kernel_variant(h, variant):
     _check(load().cld_set_kernel_variant(h, variant))
+
+
+def cld_set_grad_checkpoint(h, interval):
+    _check(load().cld_set_grad_checkpoint(h, interval))
 
 
 def cld_autotune(h, M, reps=3):

@@ -97,6 +97,11 @@ class CsrLogdet:
         g = B.cld_grad(self.h, n, M, seed, G)
         return g, G
 
+    def set_grad_checkpoint(self, interval: int):
+        """0: grad() keeps every w_j; K >= 2: keeps checkpoint pairs every K
+        steps and recomputes segments (about 2n/K + K blocks)."""
+        B.cld_set_grad_checkpoint(self.h, interval)
+
     def set_kernel_variant(self, variant: int):
         B.cld_set_kernel_variant(self.h, variant)
 

@@ -15,11 +15,12 @@ from .api import CsrLogdet
 
 class CldLogdet(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, values, rowptr, col, n, M, seed, interval):
+    def forward(ctx, values, rowptr, col, n, M, seed, interval, checkpoint):
         dtype = {torch.float32: "f32", torch.float64: "f64", torch.bfloat16: "bf16"}[values.dtype]
         m = CsrLogdet(rowptr, col, values.detach(), dtype=dtype, device=values.device)
         try:
             m.set_interval(*interval)
+            m.set_grad_checkpoint(checkpoint)
             if ctx.needs_input_grad[0]:
                 g, G = m.grad(n, M, seed)
                 ctx.save_for_backward(G)
@@ -32,9 +33,11 @@ class CldLogdet(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         (G,) = ctx.saved_tensors
-        return (grad_out * G.double()).to(G.dtype), None, None, None, None, None, None
+        return (grad_out * G.double()).to(G.dtype), None, None, None, None, None, None, None
 
 
-def logdet(values, rowptr, col, n: int, M: int, seed: int = 0, interval=(None, None)):
-    """Differentiable estimate; ``interval`` = (a, b) enclosing the spectrum."""
-    return CldLogdet.apply(values, rowptr, col, n, M, seed, tuple(interval))
+def logdet(values, rowptr, col, n: int, M: int, seed: int = 0, interval=(None, None), checkpoint: int = 0):
+    """Differentiable estimate; ``interval`` = (a, b) enclosing the spectrum;
+    ``checkpoint`` = 0 keeps every w_j for the backward, K >= 2 keeps pairs
+    every K steps and recomputes (see cld_set_grad_checkpoint)."""
+    return CldLogdet.apply(values, rowptr, col, n, M, seed, tuple(interval), int(checkpoint))

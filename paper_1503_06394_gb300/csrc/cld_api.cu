@@ -77,6 +77,7 @@ struct cld_ctx {
     bool have_interval = false;
 
     int impl = 1;  // recurrence-step inner loop (see step_kernel.cuh)
+    int ckpt = 0;  // gradient checkpoint interval K (0: keep every w_j)
 
     // batch (nb > 0): block-diagonal super matrix, blocks [blk_rows[b], blk_rows[b+1])
     int nb = 0;
@@ -110,7 +111,8 @@ struct cld_ctx {
 struct Layout {
     size_t params, result, flags, rowptrT, colT, valT, tscratch, run;  // fixed part
     size_t coeffs, coef_scratch, T, gamma_p, tpart, gpart, vbits, W[3], Y, lanczos, total;
-    size_t Wall, lam[3], H;  // gradient: w_1..w_n, the adjoint ring, per-entry sums
+    size_t Wall, lam[3], H;  // gradient: w_1..w_n (or checkpoints + a segment), the adjoint ring, per-entry sums
+    int nseg, ckK;           // checkpointed gradient: segments of w_1..w_{n-1}, their length K (0: every w_j kept)
     size_t blk_rows, tile_start, tiles, bprm, ab, bres;  // batches
     size_t xt[2];            // dense: BF16 splits of w_j, [3][panel][dx], double-buffered
     int64_t dx;
@@ -193,7 +195,17 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
     const size_t lz = align_up((size_t)5 * h->d * 8) + align_up((size_t)(8000 + L.ggrid + 64) * 8);
     if (lz > 3 * wb) { L.lanczos = o; o += lz; } else { L.lanczos = L.W[0]; }
     if (with_grad) {
-        L.Wall = o; o += (size_t)(nn > 0 ? nn : 1) * wb;
+        if (h->ckpt >= 2 && nn >= 2) {
+            // checkpoint pairs (w_{sK-1}, w_{sK}) for 1 <= s < nseg, then K segment buffers
+            L.ckK = h->ckpt;
+            L.nseg = (nn - 1 + L.ckK - 1) / L.ckK;
+            const int seglen = L.ckK < nn - 1 ? L.ckK : nn - 1;  // longest segment
+            L.Wall = o; o += (size_t)(2 * (L.nseg - 1) + seglen) * wb;
+        } else {
+            L.ckK = 0;
+            L.nseg = 0;
+            L.Wall = o; o += (size_t)(nn > 0 ? nn : 1) * wb;
+        }
         for (int i = 0; i < 3; ++i) { L.lam[i] = o; o += wb; }
         L.H = o; o += align_up((size_t)h->nnz * 4);
     }
@@ -209,16 +221,39 @@ static cld_status check_handle(cld_handle h) {
     return CLD_OK;
 }
 
-// Buffer of w_m (m >= 1): the 3-buffer ring, or (store_all) buffer m-1 of Wall.
-static float* wbuf(cld_ctx* h, const Layout& L, int m, bool store_all) {
-    if (store_all) return reinterpret_cast<float*>(h->ws + L.Wall + (size_t)(m - 1) * (L.W[1] - L.W[0]));
+// Where w_m (m >= 1) lives during a run.
+//   kMapRing: the 3-buffer ring W[m % 3];
+//   kMapAll:  buffer m-1 of Wall (gradient keeping every w_j);
+//   kMapCkpt: the ring, except w_{sK-1} and w_{sK} (1 <= s < nseg), which go
+//             to checkpoint pair s-1 at the start of Wall (checkpointed gradient);
+//   kMapSeg:  w_lo .. w_hi of a recomputed segment in the K buffers after the
+//             checkpoint pairs; its inputs w_{lo-2}, w_{lo-1} in their pair.
+enum { kMapRing = 0, kMapAll = 1, kMapCkpt = 2, kMapSeg = 3 };
+struct WMap {
+    int mode;
+    int lo;  // kMapSeg: first index of the segment
+};
+
+static float* wbuf(cld_ctx* h, const Layout& L, int m, const WMap& wm) {
+    const size_t wb = L.W[1] - L.W[0];
+    auto blk = [&](size_t i) { return reinterpret_cast<float*>(h->ws + L.Wall + i * wb); };
+    if (wm.mode == kMapAll) return blk((size_t)(m - 1));
+    if (wm.mode == kMapSeg && m >= wm.lo) return blk((size_t)(2 * (L.nseg - 1) + (m - wm.lo)));
+    if (wm.mode == kMapSeg || wm.mode == kMapCkpt) {
+        const int K = L.ckK;
+        const int r = m % K, sidx = (m + 1) / K;
+        if (m >= K - 1 && (r == K - 1 || r == 0) && sidx >= 1 && sidx <= L.nseg - 1)
+            return blk((size_t)(2 * (sidx - 1) + (r == 0 ? 1 : 0)));
+    }
     return at<float>(h, L.W[m % 3]);
 }
 
-// Enqueues the probe signs and the n recurrence steps of panel pk, then the
-// moment reduction of that panel.  Counts launches.
-static cld_status enqueue_panel_forward(cld_ctx* h, const Layout& L, int n, int M, int pk, bool store_all,
-                                        int* launches, int* step_launches) {
+// Enqueues recurrence steps j0 <= j < j1 of panel pk (step j writes w_{j+1}
+// from w_j and w_{j-1}; w_0 = v, the panel's signs, already in place) with
+// the buffers of `wm`.  Counts launches; `events` records the profiling
+// events around the general steps.
+static cld_status enqueue_steps(cld_ctx* h, const Layout& L, int n, int M, int pk, int j0, int j1, const WMap& wm,
+                                bool events, int* launches, int* step_launches) {
     Params* prm = at<Params>(h, L.params);
     double* tpart = at<double>(h, L.tpart);
     uint32_t* vbits = at<uint32_t>(h, L.vbits);
@@ -229,20 +264,18 @@ static cld_status enqueue_panel_forward(cld_ctx* h, const Layout& L, int n, int 
     const void* valT = general ? at<void>(h, L.valT) : h->val;
     const int pbase = pk * kMaxPanel;
     const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
-    CUDA_TRY(launch_probe_bits(h->d, L.nw, (uint32_t)pk, prm, vbits, L.ggrid, h->stream));
-    ++*launches;
     StepArgs a{};
     a.d = h->d;
     a.vbits = vbits;
     a.prm = prm;
     a.mreal = mreal;
     a.impl = h->impl;
-    for (int j = 0; j < n; ++j) {
+    for (int j = j0; j < j1; ++j) {
         // w_{j+1} <- step j; w_j and w_{j-1} from the previous steps (w_0 = v).
-        if (h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
-        const float* wj = j >= 1 ? wbuf(h, L, j, store_all) : nullptr;
-        const float* wjm = j >= 2 ? wbuf(h, L, j - 1, store_all) : nullptr;
-        float* wout = wbuf(h, L, j + 1, store_all);
+        if (events && h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
+        const float* wj = j >= 1 ? wbuf(h, L, j, wm) : nullptr;
+        const float* wjm = j >= 2 ? wbuf(h, L, j - 1, wm) : nullptr;
+        float* wout = wbuf(h, L, j + 1, wm);
         a.tpart = tpart + (size_t)j * L.grid * L.panel;
         StepKind kind;
         if (general) {
@@ -265,10 +298,24 @@ static cld_status enqueue_panel_forward(cld_ctx* h, const Layout& L, int n, int 
         ++*launches;
         if (j >= 2) ++*step_launches;
     }
-    if (h->profiling && n >= 3) CUDA_TRY(cudaEventRecord(h->ev[2 * pk + 1], h->stream));
+    if (events && h->profiling && n >= 3 && j1 == n) CUDA_TRY(cudaEventRecord(h->ev[2 * pk + 1], h->stream));
+    return CLD_OK;
+}
+
+// Enqueues the probe signs and the n recurrence steps of panel pk, then the
+// moment reduction of that panel.  Counts launches.
+static cld_status enqueue_panel_forward(cld_ctx* h, const Layout& L, int n, int M, int pk, const WMap& wm,
+                                        int* launches, int* step_launches) {
+    const int pbase = pk * kMaxPanel;
+    const int mreal = (M - pbase) < L.panel ? (M - pbase) : L.panel;
+    CUDA_TRY(launch_probe_bits(h->d, L.nw, (uint32_t)pk, at<Params>(h, L.params), at<uint32_t>(h, L.vbits),
+                               L.ggrid, h->stream));
+    ++*launches;
+    cld_status st = enqueue_steps(h, L, n, M, pk, 0, n, wm, true, launches, step_launches);
+    if (st != CLD_OK) return st;
     if (n > 0) {
-        CUDA_TRY(launch_reduce_moments(tpart, n, L.grid, L.panel, mreal, M, pbase, at<double>(h, L.T),
-                                       h->stream));
+        CUDA_TRY(launch_reduce_moments(at<double>(h, L.tpart), n, L.grid, L.panel, mreal, M, pbase,
+                                       at<double>(h, L.T), h->stream));
         ++*launches;
     }
     return CLD_OK;
@@ -341,7 +388,7 @@ static cld_status enqueue_estimate(cld_ctx* h, const Layout& L, int n, int M, ui
         ++launches;
     }
     for (int pk = 0; pk < npanels; ++pk) {
-        st = enqueue_panel_forward(h, L, n, M, pk, false, &launches, &step_launches);
+        st = enqueue_panel_forward(h, L, n, M, pk, WMap{kMapRing, 0}, &launches, &step_launches);
         if (st != CLD_OK) return st;
     }
     CUDA_TRY(launch_finalize(n, M, h->d, h->kind == CLD_GENERAL ? 1 : 0, prm, at<double>(h, L.T),
@@ -824,7 +871,8 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
     const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
     float* lam[3] = {at<float>(h, L.lam[0]), at<float>(h, L.lam[1]), at<float>(h, L.lam[2])};
     for (int pk = 0; pk < npanels; ++pk) {
-        st = enqueue_panel_forward(h, L, n, M, pk, true, &launches, &step_launches);
+        const WMap fwd{L.ckK > 0 ? kMapCkpt : kMapAll, 0};
+        st = enqueue_panel_forward(h, L, n, M, pk, fwd, &launches, &step_launches);
         if (st != CLD_OK) return st;
         if (n == 0) continue;
         const int mreal = (M - pk * kMaxPanel) < L.panel ? (M - pk * kMaxPanel) : L.panel;
@@ -842,16 +890,41 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
         const int64_t full = (int64_t)adjoint_ctas_per_sm(L.panel, (int)h->dtype) * h->sms;
         const int agrid = (int)(need < full ? (need > 0 ? need : 1) : full);
-        // lambda_i lives in lam[i % 3]
-        for (int i = n; i >= 1; --i) {
+        // lambda_i lives in lam[i % 3]; reverse steps i = n, n-1, ..., 1, step
+        // i < n reading w_i
+        auto reverse_step = [&](int i, const WMap& wm) -> cld_status {
             a.ci = i;
             a.lam_out = lam[i % 3];
             a.lam_in = lam[(i + 1) % 3];
             a.lam_prev = lam[(i + 2) % 3];
-            a.w = i <= n - 1 ? wbuf(h, L, i, true) : nullptr;
+            a.w = i <= n - 1 ? wbuf(h, L, i, wm) : nullptr;
             const int mode = i == n ? 0 : i == n - 1 ? 1 : 2;
             CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, mode, agrid, h->stream, a));
             ++launches;
+            return CLD_OK;
+        };
+        if (L.ckK == 0) {
+            for (int i = n; i >= 1; --i) {
+                st = reverse_step(i, WMap{kMapAll, 0});
+                if (st != CLD_OK) return st;
+            }
+        } else {
+            // checkpointed: segment s holds w_{sK+1} .. w_{min((s+1)K, n-1)}; from
+            // the last segment down, recompute it from its checkpoint pair (or
+            // from v for s = 0), then take its reverse steps
+            st = reverse_step(n, WMap{kMapSeg, 0});
+            if (st != CLD_OK) return st;
+            for (int sg = L.nseg - 1; sg >= 0; --sg) {
+                const int lo = sg * L.ckK + 1;
+                const int hi = (sg + 1) * L.ckK < n - 1 ? (sg + 1) * L.ckK : n - 1;
+                const WMap seg{kMapSeg, lo};
+                st = enqueue_steps(h, L, n, M, pk, lo - 1, hi, seg, false, &launches, &step_launches);
+                if (st != CLD_OK) return st;
+                for (int i = hi; i >= lo; --i) {
+                    st = reverse_step(i, seg);
+                    if (st != CLD_OK) return st;
+                }
+            }
         }
         a.lam_in = lam[1 % 3];  // lambda_1
         a.lam_out = nullptr;
@@ -879,6 +952,14 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
     if (r.spectrum_bad)
         return fail(CLD_ERR_SPECTRUM, "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]",
                     r.max_ratio, h->a, h->b);
+    return CLD_OK;
+}
+
+cld_status cld_set_grad_checkpoint(cld_handle h, int interval) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (interval < 0 || interval == 1 || interval > 100000)
+        return fail(CLD_ERR_INVALID, "checkpoint interval must be 0 (keep every w_j) or in [2, 100000]");
+    h->ckpt = interval;
     return CLD_OK;
 }
 

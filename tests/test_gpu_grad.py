@@ -62,6 +62,46 @@ def test_grad_matches_oracle_adjoint(torch, kind, n, M):
     assert g == est  # cld_grad's Gamma is the forward estimate
 
 
+@pytest.mark.parametrize("n,K", [(2, 2), (3, 2), (9, 2), (9, 4), (30, 6), (30, 29), (30, 40), (60, 11)])
+def test_grad_checkpointed_equals_store_all(torch, n, K):
+    """The checkpointed reverse pass (pairs every K steps, segments recomputed)
+    gives bit-identical gradients and estimate to keeping every w_j, with a
+    smaller workspace when n is large."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    P, diag, ell, s2 = wendland_small(1024)
+    val = workloads.wendland_values(P.val, diag, ell, s2)
+    B = workloads.Csr(P.rowptr, P.col, val)
+    v32, v64 = B.stored("f32")
+    a, b = s2, s2 + float(np.max(np.add.reduceat(np.abs(v64), B.rowptr[:-1])))
+    out = {}
+    for k in (0, K):
+        m = CsrLogdet(B.rowptr, B.col, v32)
+        m.set_interval(a, b)
+        m.set_grad_checkpoint(k)
+        ws = m.reserve(n, 32, 1)
+        g, G = m.grad(n, 32, 3)
+        out[k] = (g, G.cpu().numpy(), ws)
+        m.close()
+    assert out[K][0] == out[0][0]
+    assert np.array_equal(out[K][1], out[0][1])
+    nseg = -(-(n - 1) // K)
+    if 2 * (nseg - 1) + K < n:
+        assert out[K][2] < out[0][2]
+
+
+def test_grad_checkpoint_rejects_bad_interval(torch):
+    from paper_1503_06394_gb300 import CldError, CsrLogdet
+
+    B = workloads.sparse_random_spd(100, 3, 1)
+    v32, _ = B.stored("f32")
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    for k in (1, -2):
+        with pytest.raises(CldError):
+            m.set_grad_checkpoint(k)
+    m.close()
+
+
 def test_grad_directional_finite_differences(torch):
     """sum_k G_k dir_k against (Gamma(val + h dir) - Gamma(val - h dir)) / 2h of
     the FP64 oracle on the same probes and interval."""
