@@ -75,6 +75,8 @@ __device__ __forceinline__ void adj_reduce_scatter4(float (&dt)[4], int lig, uns
 template <int MP, typename VT, int MODE>
 // 6 resident CTAs per SM (40 registers, no spills): the pass is latency bound.
 __global__ void __launch_bounds__(kThreads, 6) adjoint_kernel(const AdjArgs args) {
+    pdl_wait();  // lambda_{i+1}, lambda_{i+2}, H and w_i come from earlier kernels
+    pdl_trigger();
     constexpr int LPR = MP / 4;
     constexpr int GPW = 32 / LPR;
     constexpr int NW = MP <= 32 ? 1 : MP / 32;
@@ -173,13 +175,12 @@ __global__ void __launch_bounds__(kThreads, 6) adjoint_kernel(const AdjArgs args
 template <int MP, typename VT>
 static cudaError_t launch_adj_mp(int mode, int grid, cudaStream_t s, const AdjArgs& a) {
     switch (mode) {
-        case 0: adjoint_kernel<MP, VT, 0><<<grid, kThreads, 0, s>>>(a); break;
-        case 1: adjoint_kernel<MP, VT, 1><<<grid, kThreads, 0, s>>>(a); break;
-        case 2: adjoint_kernel<MP, VT, 2><<<grid, kThreads, 0, s>>>(a); break;
-        case 3: adjoint_kernel<MP, VT, 3><<<grid, kThreads, 0, s>>>(a); break;
+        case 0: return launch_pdl(adjoint_kernel<MP, VT, 0>, grid, 0, s, a);
+        case 1: return launch_pdl(adjoint_kernel<MP, VT, 1>, grid, 0, s, a);
+        case 2: return launch_pdl(adjoint_kernel<MP, VT, 2>, grid, 0, s, a);
+        case 3: return launch_pdl(adjoint_kernel<MP, VT, 3>, grid, 0, s, a);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 template <typename VT>

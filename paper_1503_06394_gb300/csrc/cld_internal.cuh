@@ -93,6 +93,24 @@ __device__ __forceinline__ float4 signs4(uint32_t word, int sh, float4 mask) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
+// Launches kern<<<grid, kThreads, smem, s>>>(arg) with programmatic stream
+// serialization (see pdl_wait): consecutive step launches overlap their
+// launch latency with the predecessor's tail, in streams and in graphs.
+template <typename Arg>
+cudaError_t launch_pdl(void (*kern)(Arg), int grid, int smem, cudaStream_t s, const Arg& arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 // ------------------------------------------------------------------ values
 struct bf16_t { uint16_t bits; };
 

@@ -444,24 +444,6 @@ struct StepOccupancy {
 template <int IMPL, int GATHER>
 constexpr int step_smem() { return ring_bytes(IMPL); }
 
-// Launches kern<<<grid, kThreads, smem, s>>>(arg) with programmatic stream
-// serialization (see pdl_wait): consecutive step launches overlap their
-// launch latency with the predecessor's tail, in streams and in graphs.
-template <typename Arg>
-cudaError_t launch_pdl(void (*kern)(Arg), int grid, int smem, cudaStream_t s, const Arg& arg) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = (size_t)smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, arg);
-}
-
 // Opts kernel K into `bytes` of dynamic shared memory on the current device,
 // once per device (the attribute is per device; ordinals >= 64 set it on
 // every call).  Needed above 48 KB, before the first launch or occupancy query.
