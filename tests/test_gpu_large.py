@@ -1,0 +1,73 @@
+"""Maximum sizes: more than 2^31 stored entries (64-bit row pointers and
+entry offsets in every inner-loop variant).
+
+The matrix is diagonal but stored with up to 11 entries per row (the
+diagonal and explicit zeros at columns i-5 .. i+5), d = 2e8, so nnz is about
+2.2e9 > 2^31 and every gather runs through the large-offset path while the
+answer stays exact: for a diagonal matrix the estimator equals
+sum_i p_n(At_ii) for any Rademacher probes (v_i^2 = 1), with p_n the degree-n
+Chebyshev interpolant of log (Sec. 2.1), here evaluated on the host in FP64
+from the oracle's coefficients.  Built on the device (about 40 GB)."""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_common import require_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+def test_nnz_above_2_pow_31_all_variants():
+    torch = require_gpu()
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    free, _ = torch.cuda.mem_get_info()
+    if free < 80e9:
+        pytest.skip("needs about 80 GB of free device memory")
+    d, half, n, M, a, b = 200_000_000, 5, 10, 4, 0.1, 0.9
+    table = (0.15 + 0.7 * np.arange(97) / 96.0).astype(np.float32)  # diagonal values, i -> table[i % 97]
+    dev = torch.device("cuda")
+    i = torch.arange(d, device=dev, dtype=torch.int64)
+    cnt = torch.clamp(i, max=half) + 1 + torch.clamp(d - 1 - i, max=half)
+    rowptr = torch.zeros(d + 1, device=dev, dtype=torch.int64)
+    torch.cumsum(cnt, 0, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    assert nnz > 2**31
+    del cnt
+    col = torch.empty(nnz, device=dev, dtype=torch.int32)
+    val = torch.zeros(nnz, device=dev, dtype=torch.float32)
+    diag_vals = torch.as_tensor(table, device=dev)[i % 97]
+    # entry of (row, row + off) for every valid offset, in column order
+    pos = rowptr[:-1].clone()
+    for off in range(-half, half + 1):
+        ok = (i + off >= 0) & (i + off < d)
+        idx = pos[ok]
+        col[idx] = (i[ok] + off).to(torch.int32)
+        if off == 0:
+            val[idx] = diag_vals[ok]
+        pos[ok] += 1
+        del ok, idx
+    del pos, diag_vals
+
+    # exact: sum_i p_n(At_ii) = sum over the table of (count in table slot) * p_n
+    c = oracle.cheb_coeffs(n, a, b)
+    x = (2.0 * table.astype(np.float64) - (a + b)) / (b - a)
+    T = [np.ones_like(x), x]
+    for _ in range(2, n + 1):
+        T.append(2 * x * T[-1] - T[-2])
+    pn = sum(c[j] * T[j] for j in range(n + 1))
+    counts = np.bincount(np.arange(97), minlength=97) * (d // 97) + (np.arange(97) < d % 97)
+    exact = float(np.dot(counts, pn))
+
+    for variant in range(5):
+        m = CsrLogdet(rowptr, col, val, dtype="f32")
+        m.set_kernel_variant(variant)
+        m.set_interval(a, b)
+        r = m.estimate(n, M, 1)
+        m.close()
+        print("variant %d: %.6f exact %.6f rel %.2e" % (variant, r["logdet"], exact,
+                                                        abs(r["logdet"] - exact) / abs(exact)))
+        assert abs(r["logdet"] - exact) <= 1e-5 * abs(exact)
+        assert r["stderr"] <= 1e-6 * abs(exact)  # every probe sees the same diagonal
+    del rowptr, col, val, i
+    torch.cuda.empty_cache()
