@@ -398,32 +398,20 @@ def run_ours(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def adjoint_leg(args, torch, world):
-    """Config 3: Wendland kernel matrix (1e6 points, ell = 0.002, sigma2 = 0.1),
-    n = 60, M = 32.  Times cld_estimate (forward) and cld_grad (forward storing
-    every w_j + reverse pass + gradient map) on the same matrix and probes."""
+def _forward_and_grad(K, n, M, a, b, steps, torch, checkpoint_too):
+    """CUDA-event times of cld_estimate and cld_grad on one matrix (autotuned),
+    and optionally of the checkpointed cld_grad."""
     from paper_1503_06394_gb300 import CsrLogdet
 
-    cfg = dict(workloads.CONFIGS[3])
-    if args.d:
-        cfg["npts"] = int(args.d)
-        cfg["ell"] = 0.002 * (1e6 / args.d) ** 0.5  # same expected neighbour count
-    if args.n:
-        cfg["n"] = int(args.n)
-    K = workloads.make(cfg)
     v32, _ = K.stored("f32")
-    n, M = cfg["n"], cfg["M"]
-    a = cfg["sigma2"]
-    b = float(np.max(np.add.reduceat(np.abs(v32.astype(np.float64)), K.rowptr[:-1])))
     m = CsrLogdet(K.rowptr, K.col, v32)
     m.set_interval(a, b)
-    m.autotune(n, M)
+    variant, _ = m.autotune(n, M)
     ws_all = m.reserve(n, M, 1)
     m.estimate(n, M, 0)
     m.grad(n, M, 0)
     stream = torch.cuda.current_stream()
     e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    steps = max(1, args.steps)
     torch.cuda.synchronize()
     e[0].record(stream)
     for _ in range(steps):
@@ -433,35 +421,72 @@ def adjoint_leg(args, torch, world):
         g, G = m.grad(n, M, 0)
     e[2].record(stream)
     torch.cuda.synchronize()
-    fwd = e[0].elapsed_time(e[1]) / steps
-    grd = e[1].elapsed_time(e[2]) / steps
-    # checkpointed reverse pass: pairs every K ~ sqrt(2n) steps, segments recomputed
-    kc = max(2, int(round((2 * n) ** 0.5)))
-    m.set_grad_checkpoint(kc)
-    m.ws = None
-    torch.cuda.empty_cache()
-    ws_ck = m.reserve(n, M, 1)
-    gc, Gc = m.grad(n, M, 0)
-    torch.cuda.synchronize()
-    e[2].record(stream)
-    for _ in range(steps):
+    out = {"forward_ms": e[0].elapsed_time(e[1]) / steps, "grad_ms": e[1].elapsed_time(e[2]) / steps,
+           "workspace_gb": ws_all / 1e9, "variant": variant, "logdet": r["logdet"], "grad_logdet": g}
+    if checkpoint_too:
+        # checkpointed reverse pass: pairs every K ~ sqrt(2n) steps, segments recomputed
+        kc = max(2, int(round((2 * n) ** 0.5)))
+        m.set_grad_checkpoint(kc)
+        m.ws = None
+        torch.cuda.empty_cache()
+        ws_ck = m.reserve(n, M, 1)
         gc, Gc = m.grad(n, M, 0)
-    e[3].record(stream)
-    torch.cuda.synchronize()
-    grd_ck = e[2].elapsed_time(e[3]) / steps
-    same = bool(gc == g and torch.equal(Gc, G))
+        torch.cuda.synchronize()
+        e[2].record(stream)
+        for _ in range(steps):
+            gc, Gc = m.grad(n, M, 0)
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        grd_ck = e[2].elapsed_time(e[3]) / steps
+        out["checkpointed"] = {"interval": kc, "grad_ms": grd_ck, "adjoint_forward_ratio": grd_ck / out["forward_ms"],
+                               "workspace_gb": ws_ck / 1e9, "bit_identical_to_store_all": bool(gc == g and torch.equal(Gc, G))}
+        del Gc
     m.close()
-    del m, G, Gc
+    del m, G
     torch.cuda.empty_cache()
-    return {"workload": "wendland npts=%d ell=%g sigma2=%g (nnz=%d, %.1f per row), n=%d, M=%d" % (
-                cfg["npts"], cfg["ell"], cfg["sigma2"], K.nnz, K.nnz / K.d, n, M),
-            "interval": [a, b], "forward_ms": fwd, "grad_ms": grd,
-            "adjoint_forward_ratio": grd / fwd, "reverse_over_forward": (grd - fwd) / fwd,
-            "storage": "all w_j kept in HBM (%.1f GB)" % (n * K.d * 32 * 4 / 1e9),
-            "workspace_gb": ws_all / 1e9,
-            "checkpointed": {"interval": kc, "grad_ms": grd_ck, "adjoint_forward_ratio": grd_ck / fwd,
-                             "workspace_gb": ws_ck / 1e9, "bit_identical_to_store_all": same},
-            "logdet": r["logdet"], "grad_logdet": g}
+    return out
+
+
+def adjoint_leg(args, torch, world):
+    """Config 3: Wendland kernel matrix (1e6 points, ell = 0.002, sigma2 = 0.1),
+    n = 60, M = 32.  Times cld_estimate (forward) and cld_grad (forward storing
+    every w_j + reverse pass + gradient map, and the checkpointed form) on the
+    same matrix and probes, with the points numbered by cell of side ell
+    (neighbours at nearby indices); the forward and gradient are also timed
+    with the points numbered as drawn (the same matrix up to a permutation)."""
+    cfg = dict(workloads.CONFIGS[3])
+    if args.d:
+        cfg["npts"] = int(args.d)
+        cfg["ell"] = 0.002 * (1e6 / args.d) ** 0.5  # same expected neighbour count
+    if args.n:
+        cfg["n"] = int(args.n)
+    n, M = cfg["n"], cfg["M"]
+    steps = max(1, args.steps)
+    res = {}
+    for order in ("cell", "random"):
+        K = workloads.make(dict(cfg, order=order))
+        _, v64 = K.stored("f32")
+        a = cfg["sigma2"]
+        b = float(np.max(np.add.reduceat(np.abs(v64), K.rowptr[:-1])))
+        res[order] = _forward_and_grad(K, n, M, a, b, steps, torch, order == "cell")
+        res[order]["interval"] = [a, b]
+        nnz, d = K.nnz, K.d
+        del K
+    c = res["cell"]
+    out = {"workload": "wendland npts=%d ell=%g sigma2=%g (nnz=%d, %.1f per row), n=%d, M=%d, points numbered by "
+                       "cell of side ell" % (cfg["npts"], cfg["ell"], cfg["sigma2"], nnz, nnz / d, n, M),
+           "interval": c["interval"], "forward_ms": c["forward_ms"], "grad_ms": c["grad_ms"],
+           "forward_variant": c["variant"],
+           "adjoint_forward_ratio": c["grad_ms"] / c["forward_ms"],
+           "reverse_over_forward": (c["grad_ms"] - c["forward_ms"]) / c["forward_ms"],
+           "storage": "all w_j kept in HBM (%.1f GB)" % (n * d * 32 * 4 / 1e9),
+           "workspace_gb": c["workspace_gb"], "checkpointed": c["checkpointed"],
+           "logdet": c["logdet"], "grad_logdet": c["grad_logdet"],
+           "random_order": {"forward_ms": res["random"]["forward_ms"], "grad_ms": res["random"]["grad_ms"],
+                            "forward_variant": res["random"]["variant"],
+                            "adjoint_forward_ratio": res["random"]["grad_ms"] / res["random"]["forward_ms"],
+                            "logdet": res["random"]["logdet"]}}
+    return out
 
 
 def batch_bytes(mats, M, s_v, general):

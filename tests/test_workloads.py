@@ -55,6 +55,23 @@ def test_wendland_and_apex_graph():
     assert ev[0] >= 1 - 1e-9 and ev[-1] <= 2 * np.max(np.diag(A)) - 1 + 1e-9
 
 
+def test_wendland_cell_order_is_a_permutation():
+    """order="cell" renumbers the same points: K_cell = P K_random P^T."""
+    Kr, pr = workloads.wendland(500, 0.08, 0.1, 4)
+    Kc, pc = workloads.wendland(500, 0.08, 0.1, 4, order="cell")
+    _canonical(Kc)
+    # the permutation that maps random-order points to cell-order points
+    key_r = {tuple(p): i for i, p in enumerate(pr)}
+    perm = np.array([key_r[tuple(p)] for p in pc])
+    assert sorted(perm.tolist()) == list(range(500))
+    np.testing.assert_array_equal(Kc.dense(), Kr.dense()[np.ix_(perm, perm)])
+    # neighbours are closer in index after the renumbering
+    def mean_span(K):
+        rows = np.repeat(np.arange(K.d), np.diff(K.rowptr))
+        return np.mean(np.abs(rows - K.col))
+    assert mean_span(Kc) < 0.5 * mean_span(Kr)
+
+
 def test_nonsymmetric_dominant_recipe():
     C = workloads.nonsymmetric_dominant(300, 3, 5)
     _canonical(C)

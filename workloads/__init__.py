@@ -31,9 +31,11 @@ Recipes
 * ``nonsymmetric_dominant(d, picks, seed)``: general non-singular C with
   ``picks`` N(0,1) off-diagonals per row at uniform columns and diagonal
   max(row abs-sum, column abs-sum) + 1.
-* ``wendland(npts, ell, sigma2, seed)``: compactly supported Wendland kernel
-  matrix K_ik = (1 - r)^4_+ (4 r + 1), r = |x_i - x_k| / ell, on uniform points
-  in the unit square, plus sigma2 on the diagonal.
+* ``wendland(npts, ell, sigma2, seed, order)``: compactly supported Wendland
+  kernel matrix K_ik = (1 - r)^4_+ (4 r + 1), r = |x_i - x_k| / ell, on uniform
+  points in the unit square, plus sigma2 on the diagonal; points numbered as
+  drawn (order="random") or by cell of side ell (order="cell", neighbours at
+  nearby indices; a symmetric permutation of the same matrix).
 * ``apex_graph(nv, extra_edges, seed)``: a simple graph with an apex vertex
   joined to every other vertex plus random extra edges; returns the reduced
   Laplacian L(i*) with the apex row and column removed.
@@ -203,10 +205,13 @@ def nonsymmetric_dominant(d: int, picks: int, seed: int) -> Csr:
                           "nonsymmetric_dominant(d=%d,picks=%d,seed=%d)" % (d, picks, seed))
 
 
-def wendland_pattern(npts: int, ell: float, seed: int):
+def wendland_pattern(npts: int, ell: float, seed: int, order: str = "random"):
     """(Csr of distances with the diagonal stored as 0, points npts x 2): all
     pairs of uniform points in the unit square closer than ell, plus the
-    diagonal, sorted rows.  Values are the pair distances."""
+    diagonal, sorted rows.  Values are the pair distances.  order="random"
+    numbers the points as drawn; order="cell" numbers them by cell of side
+    ell (row-major), so neighbours get nearby indices (the same matrix up to
+    a symmetric permutation: the same logdet)."""
     rng = np.random.default_rng(seed)
     pts = rng.random((npts, 2))
     # cell list with cells of side >= ell: neighbours lie in the 3 x 3 block
@@ -214,6 +219,11 @@ def wendland_pattern(npts: int, ell: float, seed: int):
     cx = np.minimum((pts[:, 0] * ncell).astype(np.int64), ncell - 1)
     cy = np.minimum((pts[:, 1] * ncell).astype(np.int64), ncell - 1)
     cell = cx * ncell + cy
+    if order == "cell":
+        perm = np.argsort(cell, kind="stable")
+        pts, cx, cy, cell = pts[perm], cx[perm], cy[perm], cell[perm]
+    elif order != "random":
+        raise ValueError("order must be 'random' or 'cell'")
     order = np.argsort(cell, kind="stable")
     starts = np.searchsorted(cell[order], np.arange(ncell * ncell + 1))
     rows_l, cols_l, dist_l = [], [], []
@@ -249,9 +259,9 @@ def wendland_values(dist: np.ndarray, is_diag: np.ndarray, ell: float, sigma2: f
     return np.where(is_diag, 1.0 + sigma2, (1.0 - r) ** 4 * (4.0 * r + 1.0))
 
 
-def wendland(npts: int, ell: float, sigma2: float, seed: int) -> tuple[Csr, np.ndarray]:
-    """(K + sigma2 I as Csr, points npts x 2)."""
-    P, pts = wendland_pattern(npts, ell, seed)
+def wendland(npts: int, ell: float, sigma2: float, seed: int, order: str = "random") -> tuple[Csr, np.ndarray]:
+    """(K + sigma2 I as Csr, points npts x 2); `order` as in wendland_pattern."""
+    P, pts = wendland_pattern(npts, ell, seed, order)
     rows = np.repeat(np.arange(npts), np.diff(P.rowptr))
     vals = wendland_values(P.val, rows == P.col, ell, sigma2)
     return Csr(P.rowptr, P.col, vals, "wendland(n=%d,ell=%g,sigma2=%g,seed=%d)" % (npts, ell, sigma2, seed)), pts
@@ -322,7 +332,7 @@ CONFIGS = {
 
 def make(cfg: dict) -> Csr:
     if cfg["kind"] == "wendland":
-        return wendland(cfg["npts"], cfg["ell"], cfg["sigma2"], cfg["seed"])[0]
+        return wendland(cfg["npts"], cfg["ell"], cfg["sigma2"], cfg["seed"], cfg.get("order", "random"))[0]
     if cfg["kind"] == "sparse_random_spd":
         return sparse_random_spd(cfg["d"], cfg["picks"], cfg["seed"])
     if cfg["kind"] == "grid_gmrf":
