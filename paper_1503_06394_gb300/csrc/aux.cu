@@ -325,7 +325,7 @@ __global__ void gershgorin_kernel(int64_t d, const int64_t* __restrict__ rowptr,
     }
 }
 
-__global__ void gershgorin_final_kernel(const double* partial, int nblocks, Params* prm,
+__global__ void gershgorin_final_kernel(const double* partial, int nblocks, int64_t d, Params* prm,
                                         uint32_t* flags) {
     __shared__ double shl[kThreads], shh[kThreads];
     double lo = INFINITY, hi = -INFINITY;
@@ -344,9 +344,9 @@ __global__ void gershgorin_final_kernel(const double* partial, int nblocks, Para
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double a = shl[0], b = shh[0];
+        double a = shl[0], b = shh[0];
+        const int ok = finish_interval(a, b, d) ? 1 : 0;
         set_affine(prm, a, b);
-        const int ok = (a > 0.0 && a < b && isfinite(a) && isfinite(b)) ? 1 : 0;
         prm->interval_ok = ok;
         if (!ok) atomicOr(flags, 0x100u);
     }
@@ -372,7 +372,7 @@ cudaError_t launch_gershgorin(int64_t d, const int64_t* rowptr, const int32_t* c
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    gershgorin_final_kernel<<<1, kThreads, 0, s>>>(partial, grid, prm, flags);
+    gershgorin_final_kernel<<<1, kThreads, 0, s>>>(partial, grid, d, prm, flags);
     return cudaGetLastError();
 }
 

@@ -221,9 +221,9 @@ __global__ void batch_gershgorin_kernel(const int64_t* __restrict__ blk_rows, co
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double a = shl[0], bb = shh[0];
+        double a = shl[0], bb = shh[0];
+        const int ok = finish_interval(a, bb, blk_rows[b + 1] - blk_rows[b]) ? 1 : 0;
         set_affine(bprm + b, a, bb);
-        const int ok = (a > 0.0 && a < bb && isfinite(a) && isfinite(bb)) ? 1 : 0;
         bprm[b].interval_ok = ok;
         if (!ok) atomicOr(flags, 0x100u);
     }
@@ -269,10 +269,10 @@ __global__ void batch_general_bounds_kernel(const int64_t* __restrict__ blk_rows
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        const double a = (sh[0][0] > 0.0 && sh[2][0] > 0.0) ? sh[0][0] * sh[2][0] : 0.0;
-        const double bb = sh[1][0] * sh[3][0];
+        double a = (sh[0][0] > 0.0 && sh[2][0] > 0.0) ? sh[0][0] * sh[2][0] : 0.0;
+        double bb = sh[1][0] * sh[3][0];
+        const int ok = finish_interval(a, bb, blk_rows[b + 1] - blk_rows[b]) ? 1 : 0;
         set_affine(bprm + b, a, bb);
-        const int ok = (a > 0.0 && a < bb && isfinite(a) && isfinite(bb)) ? 1 : 0;
         bprm[b].interval_ok = ok;
         if (!ok) atomicOr(flags, 0x100u);
     }

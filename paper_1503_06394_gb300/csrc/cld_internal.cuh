@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 namespace cld {
@@ -42,6 +43,24 @@ __host__ __device__ inline void set_affine(Params* p, double a, double b) {
     p->b = b;
     split_f32(2.0 / (b - a), &p->scale_hi, &p->scale_lo);
     split_f32((a + b) / (b - a), &p->shift_hi, &p->shift_lo);
+}
+
+// Finishes a computed spectral enclosure [a, b] of a matrix (or batch block)
+// of `rows` rows: an empty one gets [1, 2] (its estimate is 0 whatever the
+// interval: t_0 = d = 0 and every other moment sums over no rows); a one-point
+// spectrum (b - a <= 1e-12 b: a 1 x 1 matrix, equal diagonal entries and no
+// off-diagonals) is widened by 0.1 % on each side, which keeps it an
+// enclosure and gives the interpolation map 2/(b - a) a finite scale.
+// Returns whether 0 < a < b with both finite.
+__host__ __device__ inline bool finish_interval(double& a, double& b, int64_t rows) {
+    if (rows == 0) {
+        a = 1.0;
+        b = 2.0;
+    } else if (a > 0.0 && isfinite(a) && isfinite(b) && b - a <= 1e-12 * b) {
+        a *= 1.0 - 1e-3;
+        b *= 1.0 + 1e-3;
+    }
+    return a > 0.0 && a < b && isfinite(a) && isfinite(b);
 }
 
 // Result block in the workspace, written by the final kernel.

@@ -361,15 +361,16 @@ __global__ void dense_gershgorin_kernel(int64_t d, int64_t ld, const __nv_bfloat
     }
 }
 
-__global__ void dense_gershgorin_final_kernel(const double* partial, int nb, Params* prm, uint32_t* flags) {
+__global__ void dense_gershgorin_final_kernel(const double* partial, int nb, int64_t d, Params* prm,
+                                              uint32_t* flags) {
     if (threadIdx.x != 0) return;
     double lo = INFINITY, hi = -INFINITY;
     for (int b = 0; b < nb; ++b) {
         lo = fmin(lo, partial[2 * b]);
         hi = fmax(hi, partial[2 * b + 1]);
     }
+    const int ok = finish_interval(lo, hi, d) ? 1 : 0;
     set_affine(prm, lo, hi);
-    const int ok = (lo > 0.0 && lo < hi && isfinite(lo) && isfinite(hi)) ? 1 : 0;
     prm->interval_ok = ok;
     if (!ok) atomicOr(flags, 0x100u);
 }
@@ -377,7 +378,7 @@ __global__ void dense_gershgorin_final_kernel(const double* partial, int nb, Par
 cudaError_t launch_dense_gershgorin(int64_t d, int64_t ld, const void* B, double* partial, int grid, Params* prm,
                                     uint32_t* flags, cudaStream_t s) {
     dense_gershgorin_kernel<<<grid, kThreads, 0, s>>>(d, ld, static_cast<const __nv_bfloat16*>(B), partial);
-    dense_gershgorin_final_kernel<<<1, 32, 0, s>>>(partial, grid, prm, flags);
+    dense_gershgorin_final_kernel<<<1, 32, 0, s>>>(partial, grid, d, prm, flags);
     return cudaGetLastError();
 }
 

@@ -152,7 +152,7 @@ __global__ void general_bounds_kernel(int64_t d, const int64_t* __restrict__ row
     if (threadIdx.x < 4) partial[4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
 }
 
-__global__ void general_bounds_final_kernel(const double* partial, int nb, Params* prm, uint32_t* flags) {
+__global__ void general_bounds_final_kernel(const double* partial, int nb, int64_t d, Params* prm, uint32_t* flags) {
     if (threadIdx.x != 0) return;
     double amin = INFINITY, rmax = 0.0, bmin = INFINITY, cmax = 0.0;
     for (int b = 0; b < nb; ++b) {
@@ -161,10 +161,10 @@ __global__ void general_bounds_final_kernel(const double* partial, int nb, Param
         bmin = fmin(bmin, partial[4 * b + 2]);
         cmax = fmax(cmax, partial[4 * b + 3]);
     }
-    const double a = (amin > 0.0 && bmin > 0.0) ? amin * bmin : 0.0;
-    const double b = rmax * cmax;
+    double a = (amin > 0.0 && bmin > 0.0) ? amin * bmin : 0.0;
+    double b = rmax * cmax;
+    const int ok = finish_interval(a, b, d) ? 1 : 0;
     set_affine(prm, a, b);
-    const int ok = (a > 0.0 && a < b && isfinite(a) && isfinite(b)) ? 1 : 0;
     prm->interval_ok = ok;
     if (!ok) atomicOr(flags, 0x100u);
 }
@@ -191,7 +191,7 @@ cudaError_t launch_general_bounds(int64_t d, const int64_t* rowptr, const int32_
             break;
         default: return cudaErrorInvalidValue;
     }
-    general_bounds_final_kernel<<<1, 32, 0, s>>>(partial, grid, prm, flags);
+    general_bounds_final_kernel<<<1, 32, 0, s>>>(partial, grid, d, prm, flags);
     return cudaGetLastError();
 }
 

@@ -173,6 +173,35 @@ def test_batch_autotune_picks_tiles(torch):
         assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
 
 
+def test_batch_empty_and_single_row_blocks(torch):
+    """Blocks of 0 and 1 rows among ordinary ones, with automatic intervals:
+    an empty block gets [1, 2] and estimates exactly 0; a 1 x 1 block's
+    one-point spectrum [beta, beta] is widened by 0.1 % on each side and its
+    estimate is log beta; every block matches the oracle on the returned
+    interval."""
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    sizes = [1, 0, 5, 0, 300, 1]
+    mats = spd_mats(sizes, 31)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    a, b = bt.auto_intervals()
+    got = bt.estimate(20, 8, 3)["logdet"]
+    bt.close()
+    for i, m in enumerate(mats):
+        if m.d == 0:
+            assert (a[i], b[i]) == (1.0, 2.0) and got[i] == 0.0
+            continue
+        _, m64 = m.stored("f32")
+        if m.d == 1:
+            beta = m64[0]
+            assert np.isclose(a[i], beta * (1 - 1e-3), rtol=1e-12) and np.isclose(b[i], beta * (1 + 1e-3), rtol=1e-12)
+            assert abs(got[i] - np.log(beta)) <= 1e-6 * abs(np.log(beta)) + 1e-9
+        ref = oracle.estimate(m.rowptr, m.col, m64, a[i], b[i], 20, 8, seed=3 + i)
+        assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"]) + 1e-9
+
+
 def test_batch_rejects_off_block_columns(torch):
     from paper_1503_06394_gb300 import CldError, CsrBatchLogdet
     from paper_1503_06394_gb300 import _binding as Bd

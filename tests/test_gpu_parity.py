@@ -232,6 +232,28 @@ def test_degenerate_inputs(torch):
     m.close()
 
 
+@pytest.mark.parametrize("d", [1, 50])
+def test_auto_interval_one_point_spectrum(torch, d):
+    """A diagonal matrix with equal entries: Gershgorin gives [beta, beta]; the
+    automatic interval is widened by 0.1 % on each side and the estimate is
+    d log beta (every probe sees the same diagonal)."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    beta = np.float32(0.37)
+    rowptr = np.arange(d + 1, dtype=np.int64)
+    col = np.arange(d, dtype=np.int32)
+    val = np.full(d, beta, dtype=np.float32)
+    m = CsrLogdet(rowptr, col, val)
+    a, b = m.auto_interval(0)
+    assert np.isclose(a, float(beta) * (1 - 1e-3), rtol=1e-12) and np.isclose(b, float(beta) * (1 + 1e-3), rtol=1e-12)
+    r = m.estimate(12, 8, 0)
+    m.close()
+    exact = d * np.log(float(beta))
+    assert abs(r["logdet"] - exact) <= 1e-6 * abs(exact)
+    ref = oracle.estimate(rowptr, col, val.astype(np.float64), a, b, 12, 8, seed=0)
+    assert abs(r["logdet"] - ref["gamma"]) <= 1e-6 * abs(ref["gamma"])
+
+
 def test_malformed_csr_rejected(torch):
     from paper_1503_06394_gb300 import CldError, CsrLogdet
     from paper_1503_06394_gb300 import _binding as Bd
