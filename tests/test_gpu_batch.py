@@ -173,6 +173,24 @@ def test_batch_autotune_picks_tiles(torch):
         assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
 
 
+def test_batch_two_panels(torch):
+    """M = 140 probes: two panels (128 + 12), each block against the oracle."""
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = spd_mats([700, 40, 1500], 51)
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    a, b = intervals(mats)
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    bt.set_intervals(a, b)
+    got = bt.estimate(12, 140, 6)["logdet"]
+    bt.close()
+    for i, m in enumerate(mats):
+        _, m64 = m.stored("f32")
+        ref = oracle.estimate(m.rowptr, m.col, m64, a[i], b[i], 12, 140, seed=6 + i)
+        assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
+
+
 def test_batch_empty_and_single_row_blocks(torch):
     """Blocks of 0 and 1 rows among ordinary ones, with automatic intervals:
     an empty block gets [1, 2] and estimates exactly 0; a 1 x 1 block's

@@ -42,7 +42,7 @@ def wendland_small(d=2048, seed=5, sigma2=0.1):
 
 
 @pytest.mark.parametrize("kind", ["random", "wendland"])
-@pytest.mark.parametrize("n,M", [(1, 4), (2, 8), (7, 16), (30, 32), (20, 64), (5, 128), (6, 3)])
+@pytest.mark.parametrize("n,M", [(1, 4), (2, 8), (7, 16), (30, 32), (20, 64), (5, 128), (6, 3), (8, 140)])
 def test_grad_matches_oracle_adjoint(torch, kind, n, M):
     if kind == "random":
         B = workloads.sparse_random_spd(1500, 3, 31)
