@@ -790,7 +790,7 @@ def main():
     ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency", "gmrf"], default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
-    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4],
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="pin the recurrence-step inner-loop variant instead of autotuning it")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -275,9 +275,13 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *      memory with cp.async while the group consumes the previous row (for
  *      short rows, e.g. stencils, where dependent loads otherwise serialise);
  *      entries past the 5th are gathered directly;
- *   4: as 3 with the first 8 entries staged (more shared memory, 2 CTAs/SM).
+ *   4: as 3 with the first 8 entries staged (more shared memory, 2 CTAs/SM);
+ *   5: wide lanes: each lane owns 8 consecutive probes of a row (256-bit
+ *      gathers) and keeps 4 stored entries in flight, paying the per-entry
+ *      index, value and address work once per 8 probes (panels of at least 8
+ *      probes; a batch handle runs variant 0 for it).
  * The default at creation is 3 when the matrix holds at most 6 stored entries
- * per row on average, else 4 (batches: 0).  The variant also sets the grid
+ * per row on average, else 5 (batches: 0).  The variant also sets the grid
  * size, so the last bits of the moments (their summation order) can change
  * with it.
  * Errors: CLD_ERR_INVALID for an unknown variant. */

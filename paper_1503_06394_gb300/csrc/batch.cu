@@ -105,6 +105,7 @@ static cudaError_t launch_batch_mp(StepKind kind, int grid, cudaStream_t s, cons
         case 2: return launch_batch_impl<MP, VT, 2>(kind, grid, s, a);
         case 3: return launch_batch_impl<MP, VT, 3>(kind, grid, s, a);
         case 4: return launch_batch_impl<MP, VT, 4>(kind, grid, s, a);
+        case 5: return launch_batch_impl<MP, VT, 0>(kind, grid, s, a);  // no wide-lane batch kernel
         default: return cudaErrorInvalidValue;
     }
 }

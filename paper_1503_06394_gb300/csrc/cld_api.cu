@@ -119,9 +119,9 @@ struct Layout {
     int panel, nw, grid, ggrid;
 };
 
-// Inner-loop variant at creation: the shared-memory rings (3 stages the
-// first 5 entries of a row, 4 the first 8).
-static int default_impl(int64_t d, int64_t nnz) { return nnz <= 6 * d ? 3 : 4; }
+// Inner-loop variant at creation: the shared-memory ring staging the first
+// 5 entries of a row (3) for short rows, the wide lanes (5) otherwise.
+static int default_impl(int64_t d, int64_t nnz) { return nnz <= 6 * d ? 3 : 5; }
 
 static int panel_for_dense(int M) { return M <= 32 ? 32 : M <= 64 ? 64 : 128; }
 
@@ -1212,7 +1212,8 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
                 return ust;
             }
         }
-        for (int v = 0; v < kNumStepImpls; ++v) {
+        // variant 5 (wide lanes) has no batch kernel
+        for (int v = 0; v < (h->nb > 0 ? 5 : kNumStepImpls); ++v) {
             h->impl = v;
             const Layout L = make_layout(h, 2, M, 0);
             if (L.total > h->ws_bytes) continue;
@@ -1310,7 +1311,8 @@ cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row
     if (M < 1) return fail(CLD_ERR_INVALID, "M >= 1");
     const Layout L = make_layout(h, 1, M, 0);
     if (panel) *panel = L.panel;
-    if (lanes_per_row) *lanes_per_row = L.panel / 4;
+    // 4 probes per lane; 8 with the wide lanes (variant 5, panels of 8 or more)
+    if (lanes_per_row) *lanes_per_row = (h->impl == 5 && h->nb == 0 && L.panel >= 8) ? L.panel / 8 : L.panel / 4;
     if (ctas) *ctas = L.grid;
     if (threads) *threads = kThreads;
     return CLD_OK;

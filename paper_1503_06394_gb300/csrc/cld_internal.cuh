@@ -176,7 +176,7 @@ struct StepArgs {
     int impl;                // inner-loop variant (0..kNumStepImpls-1, see step_kernel.cuh)
 };
 
-constexpr int kNumStepImpls = 5;
+constexpr int kNumStepImpls = 6;
 
 enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
                 kStepFirstFromFloat = 5 };

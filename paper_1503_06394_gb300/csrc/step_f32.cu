@@ -1,6 +1,6 @@
 // Recurrence-step kernels for f32 stored values (one translation unit per
 // value type so the instantiations compile in parallel).
-#include "step_kernel.cuh"
+#include "step_launch.cuh"
 
 namespace cld {
 

@@ -539,86 +539,4 @@ __global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value)
     }
 }
 
-template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>
-cudaError_t launch_one_step(int grid, cudaStream_t s, const StepArgs& a) {
-    constexpr auto kern = step_kernel<MP, VT, GATHER, PREV, EPI, IMPL>;
-    constexpr int smem = step_smem<IMPL, GATHER>();
-    cudaError_t e = smem_opt_in<kern>(smem);
-    if (e != cudaSuccess || grid == 0) return e;  // grid 0: opt in only
-    return launch_pdl(kern, grid, smem, s, a);
-}
-
-template <int MP, typename VT, int IMPL>
-cudaError_t launch_step_impl(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
-    switch (kind) {
-        case kStepFirst: return launch_one_step<MP, VT, 1, 0, 1, IMPL>(grid, s, a);
-        case kStepSecond: return launch_one_step<MP, VT, 0, 1, 1, IMPL>(grid, s, a);
-        case kStepGeneral: return launch_one_step<MP, VT, 0, 2, 1, IMPL>(grid, s, a);
-        case kProdBits: return launch_one_step<MP, VT, 1, 0, 0, IMPL>(grid, s, a);
-        case kProdFloat: return launch_one_step<MP, VT, 0, 0, 0, IMPL>(grid, s, a);
-        case kStepFirstFromFloat: return launch_one_step<MP, VT, 0, 0, 1, IMPL>(grid, s, a);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int MP, typename VT>
-cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
-    switch (a.impl) {
-        case 0: return launch_step_impl<MP, VT, 0>(kind, grid, s, a);
-        case 1: return launch_step_impl<MP, VT, 1>(kind, grid, s, a);
-        case 2: return launch_step_impl<MP, VT, 2>(kind, grid, s, a);
-        case 3: return launch_step_impl<MP, VT, 3>(kind, grid, s, a);
-        case 4: return launch_step_impl<MP, VT, 4>(kind, grid, s, a);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <typename VT>
-cudaError_t launch_step_vt(int panel, StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
-    switch (panel) {
-        case 4: return launch_step_mp<4, VT>(kind, grid, s, a);
-        case 8: return launch_step_mp<8, VT>(kind, grid, s, a);
-        case 16: return launch_step_mp<16, VT>(kind, grid, s, a);
-        case 32: return launch_step_mp<32, VT>(kind, grid, s, a);
-        case 64: return launch_step_mp<64, VT>(kind, grid, s, a);
-        case 128: return launch_step_mp<128, VT>(kind, grid, s, a);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
-template <int MP, typename VT, int IMPL>
-int ctas_per_sm_impl() {
-    constexpr auto kern = step_kernel<MP, VT, 0, 2, 1, IMPL>;
-    constexpr int smem = step_smem<IMPL, 0>();
-    int n = 0;
-    if (smem_opt_in<kern>(smem) != cudaSuccess) return 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kThreads, smem) != cudaSuccess) return 1;
-    return n > 0 ? n : 1;
-}
-
-template <int MP, typename VT>
-int ctas_per_sm_mp(int impl) {
-    switch (impl) {
-        case 0: return ctas_per_sm_impl<MP, VT, 0>();
-        case 1: return ctas_per_sm_impl<MP, VT, 1>();
-        case 2: return ctas_per_sm_impl<MP, VT, 2>();
-        case 3: return ctas_per_sm_impl<MP, VT, 3>();
-        case 4: return ctas_per_sm_impl<MP, VT, 4>();
-        default: return 1;
-    }
-}
-
-template <typename VT>
-int ctas_per_sm_vt(int panel, int impl) {
-    switch (panel) {
-        case 4: return ctas_per_sm_mp<4, VT>(impl);
-        case 8: return ctas_per_sm_mp<8, VT>(impl);
-        case 16: return ctas_per_sm_mp<16, VT>(impl);
-        case 32: return ctas_per_sm_mp<32, VT>(impl);
-        case 64: return ctas_per_sm_mp<64, VT>(impl);
-        case 128: return ctas_per_sm_mp<128, VT>(impl);
-        default: return 1;
-    }
-}
-
 }  // namespace cld

@@ -39,7 +39,7 @@ def intervals(mats, general=False):
 SIZES = [1, 2, 31, 32, 33, 300, 1024, 1025, 4000, 7, 2047, 5000, 13, 600]
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_batch_spd_matches_single_and_oracle(torch, variant):
     from paper_1503_06394_gb300 import CsrBatchLogdet, CsrLogdet
 

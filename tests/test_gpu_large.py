@@ -59,7 +59,7 @@ def test_nnz_above_2_pow_31_all_variants():
     counts = np.bincount(np.arange(97), minlength=97) * (d // 97) + (np.arange(97) < d % 97)
     exact = float(np.dot(counts, pn))
 
-    for variant in range(5):
+    for variant in range(6):
         m = CsrLogdet(rowptr, col, val, dtype="f32")
         m.set_kernel_variant(variant)
         m.set_interval(a, b)
