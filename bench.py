@@ -317,13 +317,13 @@ def run_ours(args, rank, world):
         iv16 = interval
         if iv16 is None:
             iv16 = m16.auto_interval(0)
-        m16.autotune(n, M)
+        v16, _ = m16.autotune(n, M)
         bg16, bmin16, _ = algorithmic_bytes_per_step(B, M, 2)
         bg16 = bmin16 if args.config == 1 else bg16
         ms16, k16, _, _, _ = time_estimates(m16, n, M, seed, interval, args.steps, max(1, args.warmup - 1), torch, world)
         m16.set_interval(*iv16)
         r16 = m16.estimate(n, M, cfg["probe_seed"], details=True)
-        bf16 = {"value": world * n * bg16 / (ms16 / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms16,
+        bf16 = {"value": world * n * bg16 / (ms16 / 1e3) / 1e9, "unit": "GB/s", "ms_per_step": ms16, "variant": v16,
                 "kernel_ms": k16, "logdet": r16["logdet"], "gamma_p0": float(r16["gamma_p"][0]),
                 "vs_fp32_time": ms16 / ms_per_step}
         m16.close()
@@ -757,13 +757,16 @@ def profiled_traffic(args, B, variant):
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "step_kernel_config2_traffic.md")
-    src = os.path.join(ROOT, "paper_1503_06394_gb300", "csrc", "step_kernel.cuh")
+    csrc = os.path.join(ROOT, "paper_1503_06394_gb300", "csrc")
     if args.config != 2 or args.d or args.dtype != "f32" or not os.path.exists(path):
         return None
     text = open(path).read()
-    want = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for name in ("step_kernel.cuh", "step_wide.cuh"):  # the device code of every variant
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    want = h.hexdigest()
     vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())
-    if vals.get("step_kernel_sha256", "").strip() != want:
+    if vals.get("step_kernels_sha256", "").strip() != want:
         return None
     try:
         return float(vals["traffic_bytes_per_launch_v%d" % variant].strip())

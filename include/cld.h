@@ -281,7 +281,7 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *      index, value and address work once per 8 probes (panels of at least 8
  *      probes; a batch handle runs variant 0 for it).
  * The default at creation is 3 when the matrix holds at most 6 stored entries
- * per row on average, else 5 (batches: 0).  The variant also sets the grid
+ * per row on average, else 4 below d = 1e5 and 5 from there (batches: 0).  The variant also sets the grid
  * size, so the last bits of the moments (their summation order) can change
  * with it.
  * Errors: CLD_ERR_INVALID for an unknown variant. */

@@ -120,8 +120,10 @@ struct Layout {
 };
 
 // Inner-loop variant at creation: the shared-memory ring staging the first
-// 5 entries of a row (3) for short rows, the wide lanes (5) otherwise.
-static int default_impl(int64_t d, int64_t nnz) { return nnz <= 6 * d ? 3 : 5; }
+// 5 entries of a row (3) for short rows; otherwise the ring staging 8 (4) for
+// small matrices, where a step is one short burst of rows and latency counts,
+// and the wide lanes (5) from d = 1e5 up, where throughput does.
+static int default_impl(int64_t d, int64_t nnz) { return nnz <= 6 * d ? 3 : d < 100000 ? 4 : 5; }
 
 static int panel_for_dense(int M) { return M <= 32 ? 32 : M <= 64 ? 64 : 128; }
 
