@@ -16,7 +16,7 @@
 // mapped through the transpose at the end (no extra gathers).
 #include <math.h>
 
-#include "cld_internal.cuh"
+#include "step_wide.cuh"
 
 namespace cld {
 
@@ -172,6 +172,146 @@ __global__ void __launch_bounds__(kThreads, 6) adjoint_kernel(const AdjArgs args
     }
 }
 
+// The same reverse step with wide lanes (the forward's variant 5): each lane
+// owns 8 consecutive probes of a row (LPR = P / 8 lanes per row, P >= 8),
+// gathers lambda_{i+1} rows with 256-bit loads, and forms its 8-probe share
+// of each entry's dot product before the reduce-scatter over the row's lanes.
+template <int MP, typename VT, int MODE>
+__global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs args) {
+    pdl_wait();  // lambda_{i+1}, lambda_{i+2}, H and w_i come from earlier kernels
+    pdl_trigger();
+    static_assert(MP >= 8, "wide lanes need at least 8 probes per panel");
+    constexpr int PPL = 8;
+    constexpr int LPR = MP / PPL;
+    constexpr int RPW = 32 / LPR;
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    constexpr int WPB = kThreads / 32;
+    constexpr int U = 4;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int sub = lane % LPR;
+    const int g_in_w = lane / LPR;
+    const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g_in_w * LPR));
+    const int64_t gid = ((int64_t)blockIdx.x * WPB + warp) * RPW + g_in_w;
+    const int64_t ngroups = (int64_t)gridDim.x * WPB * RPW;
+    const int q0 = sub * PPL, wsel = q0 >> 5, bsh = q0 & 31;
+    float mk[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) mk[q] = q0 + q < args.mreal ? 1.f : 0.f;
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
+    const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
+    const float ci = MODE == 3 ? 0.f : (float)args.coeffs[args.ci];
+    const float hfac = MODE == 3 ? 1.f : 2.f;
+
+    for (int64_t row = gid; row < args.d; row += ngroups) {
+        float v[PPL];
+        signs8(__ldg(args.vbits + row * NW + wsel), bsh, mk, v);
+        if (MODE == 0) {
+            st4(args.lam_out + row * MP + q0, make_float4(ci * v[0], ci * v[1], ci * v[2], ci * v[3]));
+            st4(args.lam_out + row * MP + q0 + 4, make_float4(ci * v[4], ci * v[5], ci * v[6], ci * v[7]));
+            continue;
+        }
+        float wk[PPL];
+        if (MODE == 3) {
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) wk[q] = v[q];
+        } else {
+            ldg8(args.w + row * MP + q0, wk);
+        }
+        const int64_t k0 = __ldg(args.rowptr + row), k1 = __ldg(args.rowptr + row + 1);
+        float acc[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
+        for (int64_t k = k0; k < k1; k += U) {
+            // this lane's share of the H updates of the chunk, loaded up front
+            int qa, qb;
+            adj_owned_entries<LPR>(sub, qa, qb);
+            float ha = 0.f, hb = 0.f, h1[U];
+            if (LPR == 1) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) h1[u] = k + u < k1 ? args.H[k + u] : 0.f;
+            }
+            if (qa >= 0 && k + qa < k1) ha = args.H[k + qa];
+            if (qb >= 0 && k + qb < k1) hb = args.H[k + qb];
+            int c[U];
+            float a[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const bool ok = k + u < k1;
+                c[u] = ok ? __ldg(args.col + k + u) : -1;
+                a[u] = ok ? load_val(val + k + u) : 0.f;
+            }
+            float xv[U][PPL];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (c[u] >= 0) {
+                    ldg8(args.lam_in + (int64_t)c[u] * MP + q0, xv[u]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                }
+            }
+            float dt[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                float t = xv[u][0] * wk[0];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) {
+                    acc[q] = fmaf(a[u], xv[u][q], acc[q]);
+                    if (q > 0) t = fmaf(xv[u][q], wk[q], t);
+                }
+                dt[u] = t;
+            }
+            if (LPR == 1) {
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (k + u < k1) args.H[k + u] = fmaf(hfac, dt[u], h1[u]);
+            }
+            float sa, sb;
+            adj_reduce_scatter4<LPR>(dt, sub, gmask, sa, sb);
+            if (qa >= 0 && k + qa < k1) args.H[k + qa] = fmaf(hfac, sa, ha);
+            if (qb >= 0 && k + qb < k1) args.H[k + qb] = fmaf(hfac, sb, hb);
+        }
+        if (MODE == 3) continue;
+        float own[PPL];
+        ldg8(args.lam_in + row * MP + q0, own);
+        float pv[PPL];
+        if (MODE == 2) {
+            const float4 lo = __ldcs(reinterpret_cast<const float4*>(args.lam_prev + row * MP + q0));
+            const float4 hi = __ldcs(reinterpret_cast<const float4*>(args.lam_prev + row * MP + q0 + 4));
+            pv[0] = lo.x; pv[1] = lo.y; pv[2] = lo.z; pv[3] = lo.w;
+            pv[4] = hi.x; pv[5] = hi.y; pv[6] = hi.z; pv[7] = hi.w;
+        } else {
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) pv[q] = 0.f;
+        }
+        float out[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            const float y = fmaf(scale, acc[q], -shift * own[q]) + fmaf(scale_lo, acc[q], -shift_lo * own[q]);
+            out[q] = fmaf(ci, v[q], fmaf(2.f, y, -pv[q]));
+        }
+        st4(args.lam_out + row * MP + q0, make_float4(out[0], out[1], out[2], out[3]));
+        st4(args.lam_out + row * MP + q0 + 4, make_float4(out[4], out[5], out[6], out[7]));
+    }
+}
+
+template <int MP, typename VT>
+static cudaError_t launch_adj_wide_mp(int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+    if constexpr (MP >= 8) {
+        switch (mode) {
+            case 0: return launch_pdl(adjoint_kernel_wide<MP, VT, 0>, grid, 0, s, a);
+            case 1: return launch_pdl(adjoint_kernel_wide<MP, VT, 1>, grid, 0, s, a);
+            case 2: return launch_pdl(adjoint_kernel_wide<MP, VT, 2>, grid, 0, s, a);
+            case 3: return launch_pdl(adjoint_kernel_wide<MP, VT, 3>, grid, 0, s, a);
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <int MP, typename VT>
 static cudaError_t launch_adj_mp(int mode, int grid, cudaStream_t s, const AdjArgs& a) {
     switch (mode) {
@@ -184,7 +324,17 @@ static cudaError_t launch_adj_mp(int mode, int grid, cudaStream_t s, const AdjAr
 }
 
 template <typename VT>
-static cudaError_t launch_adj_vt(int panel, int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+static cudaError_t launch_adj_vt(int panel, int mode, int grid, cudaStream_t s, const AdjArgs& a, bool wide) {
+    if (wide) {
+        switch (panel) {
+            case 8: return launch_adj_wide_mp<8, VT>(mode, grid, s, a);
+            case 16: return launch_adj_wide_mp<16, VT>(mode, grid, s, a);
+            case 32: return launch_adj_wide_mp<32, VT>(mode, grid, s, a);
+            case 64: return launch_adj_wide_mp<64, VT>(mode, grid, s, a);
+            case 128: return launch_adj_wide_mp<128, VT>(mode, grid, s, a);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (panel) {
         case 4: return launch_adj_mp<4, VT>(mode, grid, s, a);
         case 8: return launch_adj_mp<8, VT>(mode, grid, s, a);
@@ -219,40 +369,46 @@ __global__ void adjoint_gather_kernel(int64_t d, const int64_t* __restrict__ row
 }
 
 template <int MP, typename VT>
-static int adj_ctas_mp() {
+static int adj_ctas_mp(bool wide) {
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0) != cudaSuccess)
-        return 1;
+    cudaError_t e;
+    if constexpr (MP >= 8) {
+        e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel_wide<MP, VT, 2>, kThreads, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0);
+    } else {
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0);
+    }
+    if (e != cudaSuccess) return 1;
     return n > 0 ? n : 1;
 }
 
 template <typename VT>
-static int adj_ctas_vt(int panel) {
+static int adj_ctas_vt(int panel, bool wide) {
     switch (panel) {
-        case 4: return adj_ctas_mp<4, VT>();
-        case 8: return adj_ctas_mp<8, VT>();
-        case 16: return adj_ctas_mp<16, VT>();
-        case 32: return adj_ctas_mp<32, VT>();
-        case 64: return adj_ctas_mp<64, VT>();
-        case 128: return adj_ctas_mp<128, VT>();
+        case 4: return adj_ctas_mp<4, VT>(false);
+        case 8: return adj_ctas_mp<8, VT>(wide);
+        case 16: return adj_ctas_mp<16, VT>(wide);
+        case 32: return adj_ctas_mp<32, VT>(wide);
+        case 64: return adj_ctas_mp<64, VT>(wide);
+        case 128: return adj_ctas_mp<128, VT>(wide);
         default: return 1;
     }
 }
 
-int adjoint_ctas_per_sm(int panel, int dtype) {
+int adjoint_ctas_per_sm(int panel, int dtype, bool wide) {
     switch (dtype) {
-        case 0: return adj_ctas_vt<float>(panel);
-        case 1: return adj_ctas_vt<bf16_t>(panel);
-        case 2: return adj_ctas_vt<double>(panel);
+        case 0: return adj_ctas_vt<float>(panel, wide);
+        case 1: return adj_ctas_vt<bf16_t>(panel, wide);
+        case 2: return adj_ctas_vt<double>(panel, wide);
         default: return 1;
     }
 }
 
-cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, bool wide) {
     switch (dtype) {
-        case 0: return launch_adj_vt<float>(panel, mode, grid, s, a);
-        case 1: return launch_adj_vt<bf16_t>(panel, mode, grid, s, a);
-        case 2: return launch_adj_vt<double>(panel, mode, grid, s, a);
+        case 0: return launch_adj_vt<float>(panel, mode, grid, s, a, wide);
+        case 1: return launch_adj_vt<bf16_t>(panel, mode, grid, s, a, wide);
+        case 2: return launch_adj_vt<double>(panel, mode, grid, s, a, wide);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -285,8 +285,10 @@ struct AdjArgs {
     const Params* prm;
     int mreal;
 };
-cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a);
-int adjoint_ctas_per_sm(int panel, int dtype);
+// wide: the wide-lane reverse step (8 probes per lane, panels of at least 8),
+// used when the forward runs variant 5.
+cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, bool wide);
+int adjoint_ctas_per_sm(int panel, int dtype, bool wide);
 cudaError_t launch_adjoint_gather(int64_t d, const int64_t* rowptr, const int32_t* col, const float* H,
                                   double gscale, float* G, uint32_t* flags, int grid, cudaStream_t s);
 

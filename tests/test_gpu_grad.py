@@ -22,10 +22,12 @@ def torch():
     return require_gpu()
 
 
-def gpu_grad(B, vals, a, b, n, M, seed, dtype="f32"):
+def gpu_grad(B, vals, a, b, n, M, seed, dtype="f32", variant=None):
     from paper_1503_06394_gb300 import CsrLogdet
 
     m = CsrLogdet(B.rowptr, B.col, vals, dtype=dtype)
+    if variant is not None:
+        m.set_kernel_variant(variant)
     m.set_interval(a, b)
     g, G = m.grad(n, M, seed)
     r = m.estimate(n, M, seed)
@@ -100,6 +102,29 @@ def test_grad_checkpoint_rejects_bad_interval(torch):
         with pytest.raises(CldError):
             m.set_grad_checkpoint(k)
     m.close()
+
+
+@pytest.mark.parametrize("kind", ["random", "wendland"])
+@pytest.mark.parametrize("n,M", [(2, 8), (7, 16), (30, 32), (20, 64), (5, 128), (8, 140), (6, 12)])
+def test_grad_wide_lanes_matches_oracle_adjoint(torch, kind, n, M):
+    """With the forward's wide lanes (variant 5) the reverse pass runs its wide
+    form too (8 probes per lane, P >= 8; 1 lane per row at P = 8)."""
+    if kind == "random":
+        B = workloads.sparse_random_spd(1500, 3, 31)
+        v32, v64 = B.stored("f32")
+        a, b = oracle.gershgorin(B.rowptr, B.col, v64)
+    else:
+        P, diag, ell, s2 = wendland_small(1024)
+        val = workloads.wendland_values(P.val, diag, ell, s2)
+        B = workloads.Csr(P.rowptr, P.col, val)
+        v32, v64 = B.stored("f32")
+        a, b = s2, s2 + float(np.max(np.add.reduceat(np.abs(v64), B.rowptr[:-1])))
+    g, G, est = gpu_grad(B, v32, a, b, n, M, seed=n + M, variant=5)
+    V = oracle.rademacher(n + M, B.d, np.arange(M))
+    Gref = oracle.grad(B.rowptr, B.col, v64, a, b, n, V)
+    scale = np.max(np.abs(Gref))
+    assert np.max(np.abs(G - Gref)) <= 2e-5 * scale + 1e-7, np.max(np.abs(G - Gref)) / scale
+    assert g == est
 
 
 def test_grad_directional_finite_differences(torch):
