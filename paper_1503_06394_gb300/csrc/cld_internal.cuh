@@ -145,6 +145,19 @@ __device__ __forceinline__ float load_val_cs(const bf16_t* p) {
     uint16_t b = __ldcs(reinterpret_cast<const unsigned short*>(p));
     return __uint_as_float(((uint32_t)b) << 16);
 }
+// A stored value in its storage type (16 bits for BF16), for loops that
+// issue their gathers before they need the value, and its FP32 conversion.
+__device__ __forceinline__ float load_raw(const float* p) { return __ldg(p); }
+__device__ __forceinline__ double load_raw(const double* p) { return __ldg(p); }
+__device__ __forceinline__ uint16_t load_raw(const bf16_t* p) {
+    return __ldg(reinterpret_cast<const unsigned short*>(p));
+}
+__device__ __forceinline__ float raw_to_float(float x) { return x; }
+__device__ __forceinline__ float raw_to_float(double x) { return (float)x; }
+__device__ __forceinline__ float raw_to_float(uint16_t b) { return __uint_as_float(((uint32_t)b) << 16); }
+template <typename VT> struct RawOf { using type = VT; };
+template <> struct RawOf<bf16_t> { using type = uint16_t; };
+
 __device__ __forceinline__ double load_val_f64(const float* p) { return (double)__ldg(p); }
 __device__ __forceinline__ double load_val_f64(const double* p) { return __ldg(p); }
 __device__ __forceinline__ double load_val_f64(const bf16_t* p) {

@@ -82,13 +82,16 @@ __global__ void __launch_bounds__(kThreads, 3) step_kernel_wide(const StepArgs a
 #pragma unroll
         for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
         for (int64_t k = k0; k < k1; k += U) {
+            // indices and raw values first, the gathers next, the value
+            // conversions only at the multiply: a 16-bit value's conversion
+            // must not hold the gathers back
             int c[U];
-            float a[U];
+            typename RawOf<VT>::type araw[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool ok = k + u < k1;
                 c[u] = ok ? __ldg(args.col + k + u) : -1;
-                a[u] = ok ? load_val(val + k + u) : 0.f;
+                araw[u] = ok ? load_raw(val + k + u) : (typename RawOf<VT>::type)0;
             }
             float xv[U][PPL];
 #pragma unroll
@@ -104,9 +107,11 @@ __global__ void __launch_bounds__(kThreads, 3) step_kernel_wide(const StepArgs a
                 }
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u)
+            for (int u = 0; u < U; ++u) {
+                const float a = raw_to_float(araw[u]);
 #pragma unroll
-                for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a[u], xv[u][q], acc[q]);
+                for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
+            }
         }
         float res[PPL];
         if (EPI == 0) {
