@@ -762,7 +762,8 @@ def profiled_traffic(args, B, variant):
         return None
     text = open(path).read()
     h = hashlib.sha256()
-    for name in ("step_kernel.cuh", "step_wide.cuh"):  # the device code of every variant
+    # the device code of every variant, its value loads and its grid sizing
+    for name in ("step_kernel.cuh", "step_wide.cuh", "cld_internal.cuh", "step_launch.cuh"):
         h.update(open(os.path.join(csrc, name), "rb").read())
     want = h.hexdigest()
     vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())

@@ -80,8 +80,10 @@ typedef enum { CLD_SPD = 0, CLD_GENERAL = 1 } cld_kind;
  *   col:    nnz int32 (device), 0 <= col < d
  *   val:    nnz values (device) of type val_dtype
  *   stream: cudaStream_t to enqueue on (NULL = legacy default stream)
- * Only host-side checks run here (sizes, NULLs, d < 2^31); the arrays are
- * checked on the device by cld_set_workspace.  Errors: CLD_ERR_INVALID. */
+ * Each array must be aligned to its element size (torch allocations are).
+ * Only host-side checks run here (sizes, NULLs, alignment, d < 2^31); the
+ * arrays are checked on the device by cld_set_workspace.
+ * Errors: CLD_ERR_INVALID. */
 CLD_API cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t* rowptr,
                           const int32_t* col, const void* val, cld_dtype val_dtype,
                           cld_kind kind, void* stream);

@@ -199,6 +199,7 @@ __global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs
 #pragma unroll
     for (int q = 0; q < PPL; ++q) mk[q] = q0 + q < args.mreal ? 1.f : 0.f;
     const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const int64_t kend = value_end<VT>(args.rowptr, args.d);
     const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
     const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
     const float ci = MODE == 3 ? 0.f : (float)args.coeffs[args.ci];
@@ -220,6 +221,7 @@ __global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs
             ldg8(args.w + row * MP + q0, wk);
         }
         const int64_t k0 = __ldg(args.rowptr + row), k1 = __ldg(args.rowptr + row + 1);
+        const bool edge = k0 == 0 || k1 == kend;
         float acc[PPL];
 #pragma unroll
         for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs
             for (int u = 0; u < U; ++u) {
                 const bool ok = k + u < k1;
                 c[u] = ok ? __ldg(args.col + k + u) : -1;
-                a[u] = ok ? load_val(val + k + u) : 0.f;
+                a[u] = ok ? __uint_as_float(load_bits(val, k + u, edge)) : 0.f;
             }
             float xv[U][PPL];
 #pragma unroll

@@ -645,6 +645,8 @@ cld_status cld_create_csr(cld_handle* out, int64_t d, int64_t nnz, const int64_t
     if (val_dtype != CLD_F32 && val_dtype != CLD_BF16 && val_dtype != CLD_F64)
         return fail(CLD_ERR_INVALID, "unknown value dtype %d", (int)val_dtype);
     if (kind != CLD_SPD && kind != CLD_GENERAL) return fail(CLD_ERR_INVALID, "unknown kind %d", (int)kind);
+    if (((uintptr_t)rowptr) % 8 || ((uintptr_t)col) % 4 || ((uintptr_t)val) % value_size(val_dtype))
+        return fail(CLD_ERR_INVALID, "CSR arrays must be aligned to their element size");
     cld_ctx* h = new (std::nothrow) cld_ctx;
     if (!h) return fail(CLD_ERR_NOMEM, "host allocation failed");
     h->d = d; h->nnz = nnz; h->rowptr = rowptr; h->col = col; h->val = val;

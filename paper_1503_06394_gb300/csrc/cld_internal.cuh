@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace cld {
 
 constexpr int kThreads = 256;   // threads per CTA of every streaming kernel
@@ -145,18 +147,36 @@ __device__ __forceinline__ float load_val_cs(const bf16_t* p) {
     uint16_t b = __ldcs(reinterpret_cast<const unsigned short*>(p));
     return __uint_as_float(((uint32_t)b) << 16);
 }
-// A stored value in its storage type (16 bits for BF16), for loops that
-// issue their gathers before they need the value, and its FP32 conversion.
-__device__ __forceinline__ float load_raw(const float* p) { return __ldg(p); }
-__device__ __forceinline__ double load_raw(const double* p) { return __ldg(p); }
-__device__ __forceinline__ uint16_t load_raw(const bf16_t* p) {
-    return __ldg(reinterpret_cast<const unsigned short*>(p));
+// FP32 bits of stored value e, for the wide-lane loops (8 probes per lane,
+// several gathers in flight).  A BF16 value is read as the aligned 4-byte word
+// that holds it and the word's other half is dropped: with 16-bit loads the
+// wide-lane step ran 13 % slower on BF16 values than on FP32 ones (the same
+// requests and sectors, longer waits on the loads); with word loads it runs
+// as fast.  (The narrower loops of variants 0-4 are the other way round: word
+// loads made their BF16 steps 10-22 % slower, so they keep load_val.)  The
+// other half lies outside the array only beside its first and its last entry,
+// so a row that holds either (`edge`) reads its values 16 bits at a time.
+__device__ __forceinline__ uint32_t load_bits(const float* v, int64_t e, bool) {
+    return __float_as_uint(__ldg(v + e));
 }
-__device__ __forceinline__ float raw_to_float(float x) { return x; }
-__device__ __forceinline__ float raw_to_float(double x) { return (float)x; }
-__device__ __forceinline__ float raw_to_float(uint16_t b) { return __uint_as_float(((uint32_t)b) << 16); }
-template <typename VT> struct RawOf { using type = VT; };
-template <> struct RawOf<bf16_t> { using type = uint16_t; };
+__device__ __forceinline__ uint32_t load_bits(const double* v, int64_t e, bool) {
+    return __float_as_uint((float)__ldg(v + e));
+}
+__device__ __forceinline__ uint32_t load_bits(const bf16_t* v, int64_t e, bool edge) {
+    const unsigned short* p = reinterpret_cast<const unsigned short*>(v + e);
+    if (edge) return (uint32_t)__ldg(p) << 16;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t w = __ldg(reinterpret_cast<const unsigned int*>(a & ~uintptr_t(3)));
+    return (a & 2) ? (w & 0xffff0000u) : (w << 16);  // little-endian: the upper half is the later value
+}
+// One past the last stored position of a CSR array (rowptr[d]; its first is
+// rowptr[0] = 0, checked when the workspace is attached), which decides the
+// `edge` rows of load_bits: k0 == 0 or k1 == value_end.  Only BF16 values
+// need it; other types get 0.
+template <typename VT>
+__device__ __forceinline__ int64_t value_end(const int64_t* rowptr, int64_t d) {
+    return std::is_same<VT, bf16_t>::value ? __ldg(rowptr + d) : 0;
+}
 
 __device__ __forceinline__ double load_val_f64(const float* p) { return (double)__ldg(p); }
 __device__ __forceinline__ double load_val_f64(const double* p) { return __ldg(p); }

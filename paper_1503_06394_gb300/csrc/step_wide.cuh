@@ -64,6 +64,7 @@ __global__ void __launch_bounds__(kThreads, 3) step_kernel_wide(const StepArgs a
     for (int q = 0; q < PPL; ++q) mk[q] = q0 + q < args.mreal ? 1.f : 0.f;
     const VT* __restrict__ val = static_cast<const VT*>(args.val);
     const int64_t* __restrict__ rowptr = args.rowptr;
+    const int64_t kend = value_end<VT>(rowptr, args.d);
 
     float scale = 1.f, scale_lo = 0.f, shift = 0.f, shift_lo = 0.f;
     if (EPI == 1) {
@@ -78,20 +79,19 @@ __global__ void __launch_bounds__(kThreads, 3) step_kernel_wide(const StepArgs a
 
     for (int64_t row = gid; row < args.d; row += ngroups) {
         const int64_t k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
+        const bool edge = k0 == 0 || k1 == kend;
         float acc[PPL];
 #pragma unroll
         for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
         for (int64_t k = k0; k < k1; k += U) {
-            // indices and raw values first, the gathers next, the value
-            // conversions only at the multiply: a 16-bit value's conversion
-            // must not hold the gathers back
+            // indices and values first, then the gathers
             int c[U];
-            typename RawOf<VT>::type araw[U];
+            uint32_t abits[U];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 const bool ok = k + u < k1;
                 c[u] = ok ? __ldg(args.col + k + u) : -1;
-                araw[u] = ok ? load_raw(val + k + u) : (typename RawOf<VT>::type)0;
+                abits[u] = ok ? load_bits(val, k + u, edge) : 0u;
             }
             float xv[U][PPL];
 #pragma unroll
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 3) step_kernel_wide(const StepArgs a
             }
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const float a = raw_to_float(araw[u]);
+                const float a = __uint_as_float(abits[u]);
 #pragma unroll
                 for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
             }

@@ -55,6 +55,12 @@ def test_host_argument_checks_without_gpu(lib):
     assert B.load().cld_create_csr(ctypes.byref(h), 4, 4, None, 1, 1, 0, 0, None) == B.CLD_ERR_INVALID
     assert B.load().cld_create_csr(ctypes.byref(h), 4, 4, 8, 8, 8, 9, 0, None) == B.CLD_ERR_INVALID
     assert B.load().cld_create_csr(ctypes.byref(h), 2**31, 4, 8, 8, 8, 0, 0, None) == B.CLD_ERR_INVALID
+    # arrays not aligned to their element size (int64, int32, FP32 / BF16)
+    assert B.load().cld_create_csr(ctypes.byref(h), 4, 4, 12, 8, 8, 0, 0, None) == B.CLD_ERR_INVALID
+    assert "aligned" in B.cld_last_error()
+    assert B.load().cld_create_csr(ctypes.byref(h), 4, 4, 8, 6, 8, 0, 0, None) == B.CLD_ERR_INVALID
+    assert B.load().cld_create_csr(ctypes.byref(h), 4, 4, 8, 8, 6, 0, 0, None) == B.CLD_ERR_INVALID
+    assert B.load().cld_create_csr(ctypes.byref(h), 4, 4, 8, 8, 7, 1, 0, None) == B.CLD_ERR_INVALID
     assert B.load().cld_set_interval(None, 0.1, 1.0) == B.CLD_ERR_INVALID
     assert B.load().cld_estimate(None, 3, 3, 0, None, None, None) == B.CLD_ERR_INVALID
     assert B.load().cld_version().startswith(b"libcld")

@@ -127,6 +127,41 @@ def test_grad_wide_lanes_matches_oracle_adjoint(torch, kind, n, M):
     assert g == est
 
 
+@pytest.mark.parametrize("variant", [0, 5])
+@pytest.mark.parametrize("M", [8, 32])
+def test_grad_bf16_values_at_either_word_half(torch, variant, M):
+    """The wide reverse step (taken when the forward runs variant 5) reads
+    BF16 values as the 4-byte words that hold them, the narrow one 16 bits at
+    a time: either way the gradient of a BF16-valued matrix is the same bit for
+    bit whether the value array starts on a 4-byte boundary or 2 bytes past one
+    (odd entry count, so the last entry sits alone in its word), and matches
+    the oracle adjoint on the stored values."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    B = workloads.sparse_random_spd(1201, 3, 41)
+    assert B.nnz % 2 == 1
+    v16, v64 = B.stored("bf16")
+    a, b = oracle.gershgorin(B.rowptr, B.col, v64)
+    n = 12
+    t16 = torch.from_numpy(v16.view(np.int16)).cuda().view(torch.bfloat16)
+    Gs = []
+    for off in (0, 1):
+        buf = torch.zeros(B.nnz + 2, dtype=torch.bfloat16, device="cuda")
+        buf[off:off + B.nnz] = t16
+        m = CsrLogdet(B.rowptr, B.col, buf[off:off + B.nnz], dtype="bf16")
+        m.set_kernel_variant(variant)
+        m.set_interval(a, b)
+        g, G = m.grad(n, M, 7)
+        Gs.append((g, G.cpu().numpy().astype(np.float64)))
+        m.close()
+    assert Gs[0][0] == Gs[1][0]
+    assert np.array_equal(Gs[0][1], Gs[1][1])
+    V = oracle.rademacher(7, B.d, np.arange(M))
+    Gref = oracle.grad(B.rowptr, B.col, v64, a, b, n, V)
+    scale = np.max(np.abs(Gref))
+    assert np.max(np.abs(Gs[0][1] - Gref)) <= 2e-5 * scale + 1e-7
+
+
 def test_grad_directional_finite_differences(torch):
     """sum_k G_k dir_k against (Gamma(val + h dir) - Gamma(val - h dir)) / 2h of
     the FP64 oracle on the same probes and interval."""

@@ -177,6 +177,40 @@ def test_bf16_storage(torch):
     assert abs(r["logdet"] - ref64["gamma"]) <= 2e-3 * abs(ref64["gamma"])
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("M", [8, 32, 128])
+def test_bf16_values_at_either_word_half(torch, variant, M):
+    """BF16 value arrays that start on a 4-byte boundary or 2 bytes past one,
+    with an odd and an even entry count.  The wide lanes (variant 5) read a
+    BF16 value as the 4-byte word that holds it (16-bit loads for the rows that
+    hold the array's first or last entry), the other variants 16 bits at a
+    time; either way the results must not depend on where the array starts:
+    bit-identical across the two starts, and equal to the oracle on the stored
+    values."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    for d, seed in ((1001, 3), (1000, 4)):  # symmetric pattern + diagonal: nnz has the parity of d
+        B = workloads.sparse_random_spd(d, 3, seed)
+        assert B.nnz % 2 == d % 2
+        v16, v64 = B.stored("bf16")
+        a, b = oracle.gershgorin(B.rowptr, B.col, v64)
+        check(B, "bf16", 9, M, seed=M, interval=(a, b), variant=variant)
+        t16 = torch.from_numpy(v16.view(np.int16)).cuda().view(torch.bfloat16)
+        runs = []
+        for off in (0, 1):
+            buf = torch.zeros(B.nnz + 2, dtype=torch.bfloat16, device="cuda")
+            buf[off:off + B.nnz] = t16
+            vals = buf[off:off + B.nnz]
+            assert vals.data_ptr() % 4 == 2 * off
+            m = CsrLogdet(B.rowptr, B.col, vals, dtype="bf16")
+            m.set_kernel_variant(variant)
+            m.set_interval(a, b)
+            runs.append(m.estimate(9, M, M, moments=True))
+            m.close()
+        assert runs[0]["logdet"] == runs[1]["logdet"]
+        assert np.array_equal(runs[0]["t"], runs[1]["t"])
+
+
 def test_config1_full_sampled(torch):
     """GMRF 1000x1000 grid (d=1e6), n=50, M=64: all moments of probes 0, 37 and 63
     against the oracle; the estimate against the closed form within 5 stderr."""
