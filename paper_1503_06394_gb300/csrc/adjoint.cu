@@ -221,60 +221,69 @@ __global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs
             ldg8(args.w + row * MP + q0, wk);
         }
         const int64_t k0 = __ldg(args.rowptr + row), k1 = __ldg(args.rowptr + row + 1);
-        const bool edge = k0 == 0 || k1 == kend;
         float acc[PPL];
 #pragma unroll
         for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
-        for (int64_t k = k0; k < k1; k += U) {
-            // this lane's share of the H updates of the chunk, loaded up front
-            int qa, qb;
-            adj_owned_entries<LPR>(sub, qa, qb);
-            float ha = 0.f, hb = 0.f, h1[U];
-            if (LPR == 1) {
+        // the row's sweep; EDGE: 16-bit value loads (a BF16 row that holds the
+        // array's first or last entry), decided once per row (all lanes of the
+        // row's group take the same branch)
+        auto row_sweep = [&](auto edge_tag) {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            for (int64_t k = k0; k < k1; k += U) {
+                // this lane's share of the H updates of the chunk, loaded up front
+                int qa, qb;
+                adj_owned_entries<LPR>(sub, qa, qb);
+                float ha = 0.f, hb = 0.f, h1[U];
+                if (LPR == 1) {
 #pragma unroll
-                for (int u = 0; u < U; ++u) h1[u] = k + u < k1 ? args.H[k + u] : 0.f;
-            }
-            if (qa >= 0 && k + qa < k1) ha = args.H[k + qa];
-            if (qb >= 0 && k + qb < k1) hb = args.H[k + qb];
-            int c[U];
-            float a[U];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = k + u < k1;
-                c[u] = ok ? __ldg(args.col + k + u) : -1;
-                a[u] = ok ? __uint_as_float(load_bits(val, k + u, edge)) : 0.f;
-            }
-            float xv[U][PPL];
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (c[u] >= 0) {
-                    ldg8(args.lam_in + (int64_t)c[u] * MP + q0, xv[u]);
-                } else {
-#pragma unroll
-                    for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                    for (int u = 0; u < U; ++u) h1[u] = k + u < k1 ? args.H[k + u] : 0.f;
                 }
-            }
-            float dt[U];
+                if (qa >= 0 && k + qa < k1) ha = args.H[k + qa];
+                if (qb >= 0 && k + qb < k1) hb = args.H[k + qb];
+                int c[U];
+                float a[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                float t = xv[u][0] * wk[0];
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) {
-                    acc[q] = fmaf(a[u], xv[u][q], acc[q]);
-                    if (q > 0) t = fmaf(xv[u][q], wk[q], t);
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = k + u < k1;
+                    c[u] = ok ? __ldg(args.col + k + u) : -1;
+                    a[u] = ok ? __uint_as_float(load_bits(val, k + u, EDGE)) : 0.f;
                 }
-                dt[u] = t;
-            }
-            if (LPR == 1) {
+                float xv[U][PPL];
 #pragma unroll
-                for (int u = 0; u < U; ++u)
-                    if (k + u < k1) args.H[k + u] = fmaf(hfac, dt[u], h1[u]);
+                for (int u = 0; u < U; ++u) {
+                    if (c[u] >= 0) {
+                        ldg8(args.lam_in + (int64_t)c[u] * MP + q0, xv[u]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                    }
+                }
+                float dt[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    float t = xv[u][0] * wk[0];
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        acc[q] = fmaf(a[u], xv[u][q], acc[q]);
+                        if (q > 0) t = fmaf(xv[u][q], wk[q], t);
+                    }
+                    dt[u] = t;
+                }
+                if (LPR == 1) {
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        if (k + u < k1) args.H[k + u] = fmaf(hfac, dt[u], h1[u]);
+                }
+                float sa, sb;
+                adj_reduce_scatter4<LPR>(dt, sub, gmask, sa, sb);
+                if (qa >= 0 && k + qa < k1) args.H[k + qa] = fmaf(hfac, sa, ha);
+                if (qb >= 0 && k + qb < k1) args.H[k + qb] = fmaf(hfac, sb, hb);
             }
-            float sa, sb;
-            adj_reduce_scatter4<LPR>(dt, sub, gmask, sa, sb);
-            if (qa >= 0 && k + qa < k1) args.H[k + qa] = fmaf(hfac, sa, ha);
-            if (qb >= 0 && k + qb < k1) args.H[k + qb] = fmaf(hfac, sb, hb);
-        }
+        };
+        if (std::is_same<VT, bf16_t>::value && (k0 == 0 || k1 == kend))
+            row_sweep(std::true_type{});
+        else
+            row_sweep(std::false_type{});
         if (MODE == 3) continue;
         float own[PPL];
         ldg8(args.lam_in + row * MP + q0, own);

@@ -79,40 +79,48 @@ __global__ void __launch_bounds__(kThreads, 3) step_kernel_wide(const StepArgs a
 
     for (int64_t row = gid; row < args.d; row += ngroups) {
         const int64_t k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
-        const bool edge = k0 == 0 || k1 == kend;
         float acc[PPL];
 #pragma unroll
         for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
-        for (int64_t k = k0; k < k1; k += U) {
-            // indices and values first, then the gathers
-            int c[U];
-            uint32_t abits[U];
+        // the row's product; EDGE: 16-bit value loads (a BF16 row that holds
+        // the array's first or last entry), decided once per row
+        auto row_product = [&](auto edge_tag) {
+            constexpr bool EDGE = decltype(edge_tag)::value;
+            for (int64_t k = k0; k < k1; k += U) {
+                // indices and values first, then the gathers
+                int c[U];
+                uint32_t abits[U];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const bool ok = k + u < k1;
-                c[u] = ok ? __ldg(args.col + k + u) : -1;
-                abits[u] = ok ? load_bits(val, k + u, edge) : 0u;
-            }
-            float xv[U][PPL];
+                for (int u = 0; u < U; ++u) {
+                    const bool ok = k + u < k1;
+                    c[u] = ok ? __ldg(args.col + k + u) : -1;
+                    abits[u] = ok ? load_bits(val, k + u, EDGE) : 0u;
+                }
+                float xv[U][PPL];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (c[u] >= 0) {
-                    if (GATHER == 1)
-                        signs8(__ldg(args.vbits + (int64_t)c[u] * NW + wsel), bsh, mk, xv[u]);
-                    else
-                        ldg8(args.x + (int64_t)c[u] * MP + q0, xv[u]);
-                } else {
+                for (int u = 0; u < U; ++u) {
+                    if (c[u] >= 0) {
+                        if (GATHER == 1)
+                            signs8(__ldg(args.vbits + (int64_t)c[u] * NW + wsel), bsh, mk, xv[u]);
+                        else
+                            ldg8(args.x + (int64_t)c[u] * MP + q0, xv[u]);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                        for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float a = __uint_as_float(abits[u]);
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
                 }
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const float a = __uint_as_float(abits[u]);
-#pragma unroll
-                for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
-            }
-        }
+        };
+        if (std::is_same<VT, bf16_t>::value && (k0 == 0 || k1 == kend))
+            row_product(std::true_type{});
+        else
+            row_product(std::false_type{});
         float res[PPL];
         if (EPI == 0) {
 #pragma unroll
