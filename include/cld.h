@@ -270,7 +270,7 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  * variants compute the same sums in the same order):
  *   0: each lane loads 4 (column, value) pairs itself, 4 row gathers in flight;
  *   1: the lanes of a row load 8 pairs cooperatively and issue 8 row gathers
- *      back to back, the next chunk's pairs loaded ahead (default);
+ *      back to back, the next chunk's pairs loaded ahead;
  *   2: as 1 with chunks of 4 pairs (fewer registers, more resident CTAs);
  *   3: a shared-memory ring: the rows of w_j gathered by a row's first 5
  *      entries, its own row and its row of w_{j-1} are copied into shared
@@ -281,11 +281,13 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *   5: wide lanes: each lane owns 8 consecutive probes of a row (256-bit
  *      gathers) and keeps 4 stored entries in flight, paying the per-entry
  *      index, value and address work once per 8 probes (panels of at least 8
- *      probes; a batch handle runs variant 0 for it).
+ *      probes; a batch handle runs variant 0 for it).  BF16 values are read
+ *      as the aligned 4-byte words that hold them (16-bit loads in the rows
+ *      that hold the array's first or last entry).
  * The default at creation is 3 when the matrix holds at most 6 stored entries
- * per row on average, else 4 below d = 1e5 and 5 from there (batches: 0).  The variant also sets the grid
- * size, so the last bits of the moments (their summation order) can change
- * with it.
+ * per row on average, else 4 below d = 1e5 and 5 from there (batches: 0).
+ * The variant also sets the grid size, so the last bits of the moments (their
+ * summation order) can change with it.
  * Errors: CLD_ERR_INVALID for an unknown variant. */
 CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
 
