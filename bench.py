@@ -439,6 +439,8 @@ def _forward_and_grad(K, n, M, a, b, steps, torch, checkpoint_too):
         torch.cuda.synchronize()
         grd_ck = e[2].elapsed_time(e[3]) / steps
         out["checkpointed"] = {"interval": kc, "grad_ms": grd_ck, "adjoint_forward_ratio": grd_ck / out["forward_ms"],
+                               # (reverse pass + segment recomputation) / forward, the forward of cld_grad excluded
+                               "reverse_over_forward": (grd_ck - out["forward_ms"]) / out["forward_ms"],
                                "workspace_gb": ws_ck / 1e9, "bit_identical_to_store_all": bool(gc == g and torch.equal(Gc, G))}
         del Gc
     m.close()
