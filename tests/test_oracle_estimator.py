@@ -135,6 +135,34 @@ def test_basis_probes_give_exact_trace(oracle_mod):
     assert abs(g * B.d - np.sum(np.log(ev))) < 1e-6 * abs(np.sum(np.log(ev)))
 
 
+@pytest.mark.parametrize("delta,n", [(0.1, 4), (0.1, 10), (0.2, 6), (0.05, 20)])
+def test_lemma1_trace_bound(oracle_mod, delta, n):
+    """Lemma 1 (Sec. 4.1): for spec(B) in [delta, 1-delta],
+    |log det B - tr p_n(B)| <= d * (the per-eigenvalue bound).  tr p_n(B) is
+    the estimator's deterministic part, taken exactly with the d basis vectors
+    as probes; log det B comes from the eigenvalues numpy draws."""
+    d = 96
+    X = random_spd(d, 17 + n, lo=delta, hi=1.0 - delta)
+    ev = np.linalg.eigvalsh(X)
+    rowptr, col, val = csr_from_dense(X)
+    t = oracle_mod.moments(rowptr, col, val, delta, 1.0 - delta, n, np.eye(d))
+    _, g = oracle_mod.finalize(oracle_mod.cheb_coeffs(n, delta, 1.0 - delta), t)
+    err = abs(np.sum(np.log(ev)) - g * d)
+    assert err <= d * oracle_mod.chebyshev_error_bound(delta, n)
+
+
+def test_lemma2_every_probe_estimate_negative(oracle_mod):
+    """Lemma 2 at the matrix level: once n meets the lemma's condition, p_n < 0
+    on [delta, 1-delta], so p_n(B) is negative definite for spec(B) there and
+    every probe's Gamma_p = v^T p_n(B) v is negative, whatever the signs."""
+    delta = 0.1
+    n = next(k for k in range(1, 200) if oracle_mod.chebyshev_error_bound(delta, k) <= np.log(1 / (1 - delta)))
+    X = random_spd(80, 5, lo=delta, hi=1.0 - delta)
+    rowptr, col, val = csr_from_dense(X)
+    r = oracle_mod.estimate(rowptr, col, val, delta, 1.0 - delta, n, 64, seed=11)
+    assert np.all(r["gamma_p"] < 0)
+
+
 def test_spectrum_invariant(oracle_mod):
     """|t_{j,p}| <= ||v||^2 = d whenever the spectrum lies in [a, b]."""
     B = workloads.sparse_random_spd(500, 3, 9)
