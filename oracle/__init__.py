@@ -15,6 +15,11 @@ exact references that are easiest to state in numpy:
 * ``thm1_degree`` / ``thm1_samples`` -- the sufficient degree and sample count of
   Theorem 1, and ``chebyshev_error_bound`` -- the per-eigenvalue bound
   20 log(2(1/delta - 1)) / ((K-1) K^n) of Sec. 4.1.
+
+Every arithmetic function here is pinned by a CPU test against something other
+than itself (closed forms, numpy's eigensolver and slogdet, exhaustive sign
+enumeration, finite differences, cuRAND's host Philox); none is parity
+unpinned.
 """
 from __future__ import annotations
 
