@@ -283,14 +283,6 @@ def grid_laplacian_logdet(N: int, kappa2: float) -> float:
     return math.fsum(np.log(lam).ravel().tolist())
 
 
-def dense_from_csr(rowptr, col, val) -> np.ndarray:
-    d, rowptr, col, val = _csr(rowptr, col, val)
-    A = np.zeros((d, d), dtype=np.float64)
-    rows = np.repeat(np.arange(d), np.diff(rowptr))
-    np.add.at(A, (rows, col), val)
-    return A
-
-
 def chebyshev_error_bound(delta: float, n: int) -> float:
     """20 log(2(1/delta - 1)) / ((K-1) K^n), K = (sqrt(2-delta)+sqrt(delta))/(sqrt(2-delta)-sqrt(delta))
     (Sec. 4.1: the per-eigenvalue bound for log(1-x) on [delta, 1-delta])."""
