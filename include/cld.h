@@ -196,9 +196,10 @@ CLD_API cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* ro
  * runs under a fixed device-memory budget, and latency-critical loops that
  * must never block in cudaMalloc/cudaFree.  The paper has no counterpart: this
  * is the same estimate as cld_create_csr + cld_set_interval + cld_estimate
- * (CLD_SPD only), but its scratch lives in one file-scope __device__ array of
- * CLD_STATIC_SCRATCH_BYTES that every GPU which loads the library holds until
- * the process exits.
+ * (CLD_SPD only; it runs inner-loop variant 0, so the moments' last bits can
+ * differ from a handle's by summation order), but its scratch lives in one
+ * file-scope __device__ array of CLD_STATIC_SCRATCH_BYTES that every GPU which
+ * loads the library holds until the process exits.
  *   rowptr, col, val: the CSR matrix on the device, as in cld_create_csr
  *   a, b, n, M, seed: as in cld_set_interval / cld_estimate
  *   stream: cudaStream_t to enqueue on (NULL = legacy default stream)

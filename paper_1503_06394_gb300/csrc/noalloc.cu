@@ -94,7 +94,7 @@ extern "C" cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t*
     STATIC_TRY(cudaGetDevice(&dev));
     STATIC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
 
-    // sizes (same kernels, same launch shapes as cld_estimate)
+    // sizes: the per-lane inner loop (variant 0) with its cld_estimate launch shape
     int panel = 4;
     if (M >= kMaxPanel) panel = kMaxPanel;
     else while (panel < M) panel <<= 1;
