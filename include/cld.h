@@ -282,9 +282,9 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *   5: wide lanes: each lane owns 8 consecutive probes of a row (256-bit
  *      gathers) and keeps 4 stored entries in flight, paying the per-entry
  *      index, value and address work once per 8 probes (panels of at least 8
- *      probes; a batch handle runs variant 0 for it).  BF16 values are read
- *      as the aligned 4-byte words that hold them (16-bit loads in the rows
- *      that hold the array's first or last entry).
+ *      probes, else variant 0; batch handles have a wide-lane tile kernel
+ *      too).  BF16 values are read as the aligned 4-byte words that hold them
+ *      (16-bit loads in the rows that hold the array's first or last entry).
  * The default at creation is 3 when the matrix holds at most 6 stored entries
  * per row on average, else 4 below d = 1e5 and 5 from there (batches: 0).
  * The variant also sets the grid size, so the last bits of the moments (their

@@ -10,7 +10,7 @@
 // block's tiles in tile order.
 #include <math.h>
 
-#include "step_kernel.cuh"
+#include "step_wide.cuh"
 
 namespace cld {
 
@@ -77,6 +77,144 @@ __global__ void __launch_bounds__(kThreads, (StepOccupancy<IMPL, GATHER>::value)
     }
 }
 
+// The tile-queue step with wide lanes (variant 5 for batches): each lane owns
+// 8 consecutive probes of a row (P / 8 lanes per row, P >= 8), gathers row
+// slices with 256-bit loads and keeps 4 stored entries in flight; BF16 values
+// are read as the 4-byte words that hold them (16-bit loads in the rows that
+// hold the array's first or last entry).  Each row's sum is formed in entry
+// order and updated with the same operations as batch_step_kernel, so w_{j+1}
+// is identical; only the moments' summation order differs.
+template <int MP, typename VT, int GATHER, int PREV>
+__global__ void __launch_bounds__(kThreads, 3) batch_step_kernel_wide(const BatchStepArgs ba) {
+    pdl_wait();  // w_j, w_{j-1}, the signs, tiles and parameters come from earlier kernels
+    pdl_trigger();
+    static_assert(MP >= 8, "wide lanes need at least 8 probes per panel");
+    constexpr int PPL = 8;             // probes per lane
+    constexpr int LPR = MP / PPL;      // lanes per row
+    constexpr int RPW = 32 / LPR;      // rows per warp
+    constexpr int NW = MP <= 32 ? 1 : MP / 32;
+    constexpr int WPB = kThreads / 32;
+    constexpr int U = 4;               // stored entries in flight per lane
+    const StepArgs& args = ba.s;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int sub = lane % LPR;
+    const int g_in_w = lane / LPR;
+    const int gloc = warp * RPW + g_in_w;  // row group within the CTA
+    const int gcta = WPB * RPW;            // row groups per CTA
+    const int q0 = sub * PPL, wsel = q0 >> 5, bsh = q0 & 31;
+    float mk[PPL];
+#pragma unroll
+    for (int q = 0; q < PPL; ++q) mk[q] = q0 + q < args.mreal ? 1.f : 0.f;
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const int64_t* __restrict__ rowptr = args.rowptr;
+    const int64_t kend = value_end<VT>(rowptr, args.d);
+    __shared__ double red[WPB][MP];
+
+    for (int64_t t = blockIdx.x; t < ba.ntiles; t += gridDim.x) {
+        const Tile tl = ba.tiles[t];
+        const Params* P = ba.bprm + tl.blk;
+        const float scale = P->scale_hi, scale_lo = P->scale_lo, shift = P->shift_hi, shift_lo = P->shift_lo;
+        float tacc[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) tacc[q] = 0.f;
+        for (int64_t row = tl.lo + gloc; row < tl.hi; row += gcta) {
+            const int64_t k0 = __ldg(rowptr + row), k1 = __ldg(rowptr + row + 1);
+            float acc[PPL];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
+            auto row_product = [&](auto edge_tag) {
+                constexpr bool EDGE = decltype(edge_tag)::value;
+                for (int64_t k = k0; k < k1; k += U) {
+                    int c[U];
+                    uint32_t abits[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const bool ok = k + u < k1;
+                        c[u] = ok ? __ldg(args.col + k + u) : -1;
+                        abits[u] = ok ? load_bits(val, k + u, EDGE) : 0u;
+                    }
+                    float xv[U][PPL];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (c[u] >= 0) {
+                            if (GATHER == 1)
+                                signs8(__ldg(args.vbits + (int64_t)c[u] * NW + wsel), bsh, mk, xv[u]);
+                            else
+                                ldg8(args.x + (int64_t)c[u] * MP + q0, xv[u]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float a = __uint_as_float(abits[u]);
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
+                    }
+                }
+            };
+            if (std::is_same<VT, bf16_t>::value && (k0 == 0 || k1 == kend))
+                row_product(std::true_type{});
+            else
+                row_product(std::false_type{});
+            float v[PPL], own[PPL], pv[PPL], res[PPL];
+            signs8(__ldg(args.vbits + row * NW + wsel), bsh, mk, v);
+            if (PREV == 0) {
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) own[q] = v[q];
+            } else {
+                ldg8(args.own + row * MP + q0, own);
+            }
+            if (PREV == 2) {
+                const float4 lo = ldcs4(args.wprev + row * MP + q0), hi = ldcs4(args.wprev + row * MP + q0 + 4);
+                pv[0] = lo.x; pv[1] = lo.y; pv[2] = lo.z; pv[3] = lo.w;
+                pv[4] = hi.x; pv[5] = hi.y; pv[6] = hi.z; pv[7] = hi.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) pv[q] = v[q];
+            }
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                res[q] = recurrence_update1<PREV>(acc[q], own[q], pv[q], scale, scale_lo, shift, shift_lo);
+                tacc[q] = fmaf(v[q], res[q], tacc[q]);
+            }
+            st4(args.out + row * MP + q0, make_float4(res[0], res[1], res[2], res[3]));
+            st4(args.out + row * MP + q0 + 4, make_float4(res[4], res[5], res[6], res[7]));
+        }
+        // lanes with the same `sub` hold the same probes: fold them, then the
+        // warps of the CTA in a fixed order, into this tile's partials
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) {
+            double tq = tacc[q];
+#pragma unroll
+            for (int off = LPR; off < 32; off <<= 1) tq += __shfl_xor_sync(0xffffffffu, tq, off);
+            if (g_in_w == 0) red[warp][q0 + q] = tq;
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < MP; p += kThreads) {
+            double sum = 0.0;
+#pragma unroll
+            for (int w = 0; w < WPB; ++w) sum += red[w][p];
+            ba.tpart[t * MP + p] = sum;
+        }
+        __syncthreads();
+    }
+}
+
+template <int MP, typename VT>
+static cudaError_t launch_batch_wide(StepKind kind, int grid, cudaStream_t s, const BatchStepArgs& a) {
+    if (grid == 0) return cudaSuccess;  // no dynamic shared memory to opt in
+    switch (kind) {
+        case kStepFirst: return launch_pdl(batch_step_kernel_wide<MP, VT, 1, 0>, grid, 0, s, a);
+        case kStepSecond: return launch_pdl(batch_step_kernel_wide<MP, VT, 0, 1>, grid, 0, s, a);
+        case kStepGeneral: return launch_pdl(batch_step_kernel_wide<MP, VT, 0, 2>, grid, 0, s, a);
+        case kStepFirstFromFloat: return launch_pdl(batch_step_kernel_wide<MP, VT, 0, 0>, grid, 0, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int MP, typename VT, int GATHER, int PREV, int IMPL>
 static cudaError_t launch_one_batch(int grid, cudaStream_t s, const BatchStepArgs& a) {
     constexpr auto kern = batch_step_kernel<MP, VT, GATHER, PREV, IMPL>;
@@ -105,7 +243,9 @@ static cudaError_t launch_batch_mp(StepKind kind, int grid, cudaStream_t s, cons
         case 2: return launch_batch_impl<MP, VT, 2>(kind, grid, s, a);
         case 3: return launch_batch_impl<MP, VT, 3>(kind, grid, s, a);
         case 4: return launch_batch_impl<MP, VT, 4>(kind, grid, s, a);
-        case 5: return launch_batch_impl<MP, VT, 0>(kind, grid, s, a);  // no wide-lane batch kernel
+        case 5:
+            if constexpr (MP >= 8) return launch_batch_wide<MP, VT>(kind, grid, s, a);
+            else return launch_batch_impl<MP, VT, 0>(kind, grid, s, a);  // wide lanes need 8 probes
         default: return cudaErrorInvalidValue;
     }
 }

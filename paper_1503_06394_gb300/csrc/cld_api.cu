@@ -1218,8 +1218,7 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
                 return ust;
             }
         }
-        // variant 5 (wide lanes) has no batch kernel
-        for (int v = 0; v < (h->nb > 0 ? 5 : kNumStepImpls); ++v) {
+        for (int v = 0; v < kNumStepImpls; ++v) {
             h->impl = v;
             const Layout L = make_layout(h, 2, M, 0);
             if (L.total > h->ws_bytes) continue;

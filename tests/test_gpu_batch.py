@@ -67,13 +67,15 @@ def test_batch_spd_matches_single_and_oracle(torch, variant):
             assert abs(r["stderr"][k] - ref["stderr"]) <= 1e-3 * ref["stderr"] + 1e-9
 
 
-def test_batch_general_matches_oracle(torch):
+@pytest.mark.parametrize("variant", [0, 5])
+def test_batch_general_matches_oracle(torch, variant):
     from paper_1503_06394_gb300 import CsrBatchLogdet
 
     mats = [workloads.nonsymmetric_dominant(int(d), 3, 70 + i) for i, d in enumerate([3, 64, 500, 2500, 1200, 90])]
     br, S = workloads.block_diag(mats)
     s32, _ = S.stored("f32")
     bt = CsrBatchLogdet(br, S.rowptr, S.col, s32, kind="general")
+    bt.set_kernel_variant(variant)
     a, b = bt.auto_intervals()
     ea, eb = intervals(mats, general=True)
     np.testing.assert_allclose(a, ea, rtol=1e-9)
@@ -163,7 +165,7 @@ def test_batch_autotune_picks_tiles(torch):
     bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
     bt.set_intervals(a, b)
     v, ms = bt.autotune(20, 32)
-    assert v in range(5) and ms > 0
+    assert v in range(6) and ms > 0
     assert bt.tile_rows in (256, 512, 1024, 2048, 4096)
     got = bt.estimate(20, 32, 9)["logdet"]
     bt.close()
@@ -173,7 +175,8 @@ def test_batch_autotune_picks_tiles(torch):
         assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
 
 
-def test_batch_two_panels(torch):
+@pytest.mark.parametrize("variant", [0, 5])
+def test_batch_two_panels(torch, variant):
     """M = 140 probes: two panels (128 + 12), each block against the oracle."""
     from paper_1503_06394_gb300 import CsrBatchLogdet
 
@@ -182,6 +185,7 @@ def test_batch_two_panels(torch):
     s32, _ = S.stored("f32")
     a, b = intervals(mats)
     bt = CsrBatchLogdet(br, S.rowptr, S.col, s32)
+    bt.set_kernel_variant(variant)
     bt.set_intervals(a, b)
     got = bt.estimate(12, 140, 6)["logdet"]
     bt.close()
@@ -189,6 +193,45 @@ def test_batch_two_panels(torch):
         _, m64 = m.stored("f32")
         ref = oracle.estimate(m.rowptr, m.col, m64, a[i], b[i], 12, 140, seed=6 + i)
         assert abs(got[i] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
+
+
+@pytest.mark.parametrize("variant", [0, 4, 5])
+def test_batch_bf16_values_at_either_word_half(torch, variant):
+    """BF16 batches, the value array starting on a 4-byte boundary or 2 bytes
+    past one (odd entry count): the wide tile kernel reads the values as the
+    4-byte words that hold them, the others 16 bits at a time; every block
+    matches the oracle on the stored values and the two starts agree bit for
+    bit."""
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = spd_mats([1, 301, 2048, 77, 1500], 61)
+    br, S = workloads.block_diag(mats)
+    assert S.nnz % 2 == 1
+    s16, _ = S.stored("bf16")
+    a, b = [], []
+    for m in mats:
+        _, m64 = m.stored("bf16")
+        lo, hi = oracle.gershgorin(m.rowptr, m.col, m64)
+        if not hi - lo > 1e-9 * hi:
+            lo, hi = 0.5 * lo, 1.5 * hi
+        a.append(lo)
+        b.append(hi)
+    n, M, seed = 15, 16, 4
+    t16 = torch.from_numpy(s16.view(np.int16)).cuda().view(torch.bfloat16)
+    got = []
+    for off in (0, 1):
+        buf = torch.zeros(S.nnz + 2, dtype=torch.bfloat16, device="cuda")
+        buf[off:off + S.nnz] = t16
+        bt = CsrBatchLogdet(br, S.rowptr, S.col, buf[off:off + S.nnz], dtype="bf16")
+        bt.set_kernel_variant(variant)
+        bt.set_intervals(np.array(a), np.array(b))
+        got.append(bt.estimate(n, M, seed)["logdet"])
+        bt.close()
+    np.testing.assert_array_equal(got[0], got[1])
+    for k, m in enumerate(mats):
+        _, m64 = m.stored("bf16")
+        ref = oracle.estimate(m.rowptr, m.col, m64, a[k], b[k], n, M, seed=seed + k)
+        assert abs(got[0][k] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"]) + 1e-9, k
 
 
 def test_batch_empty_and_single_row_blocks(torch):
