@@ -56,7 +56,9 @@ def read_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running.
+    The raw samples go to a CSV in $CLD_CLOCKS_DIR (default: the temp dir);
+    the JSON line carries their summary."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -64,7 +66,9 @@ class ClockSampler:
 
     def __init__(self, gpu_index=0, name="clocks_bench.csv"):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", name)
+        import tempfile
+
+        self.path = os.path.join(os.environ.get("CLD_CLOCKS_DIR") or tempfile.gettempdir(), name)
         self.gpu_index = gpu_index
 
     def __enter__(self):
