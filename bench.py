@@ -66,6 +66,8 @@ class ClockSampler:
 
     def __init__(self, gpu_index=0, name="clocks_bench.csv"):
         self.proc = None
+        self.f = None
+        self.failure = None
         import tempfile
 
         self.path = os.path.join(os.environ.get("CLD_CLOCKS_DIR") or tempfile.gettempdir(), name)
@@ -75,11 +77,18 @@ class ClockSampler:
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
+        except OSError as e:
+            self.failure = "clock log not writable: %s" % e
+            return self
+        try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_index), "--query-gpu=" + self.FIELDS,
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
                                          stderr=subprocess.DEVNULL)
-        except Exception:
+        except OSError as e:
             self.proc = None
+            self.failure = "nvidia-smi unavailable: %s" % e
+            self.f.close()
+            self.f = None
         return self
 
     def __exit__(self, *a):
@@ -89,11 +98,13 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        if self.f is not None:
             self.f.close()
+            self.f = None
 
     def summary(self):
-        if self.proc is None or not os.path.exists(self.path):
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        if self.failure is not None or self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [self.failure or "nvidia-smi unavailable"]}
         sm, smax, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
@@ -242,8 +253,11 @@ def run_only(args):
 
     __graft_entry__.build()
     leg = {"dense": dense_leg, "adjoint": adjoint_leg, "paper": paper_leg, "latency": latency_leg,
-           "gmrf": gmrf_leg}[args.only]
+           "gmrf": gmrf_leg, "config1": config1_leg, "batch": batch_leg}[args.only]
     out = leg(args, torch, 1) if args.only == "adjoint" else leg(args, torch)
+    key = {"config1": "gmrf_config1"}.get(args.only, args.only)
+    if not args.no_cpu_baseline and key in ("latency", "gmrf_config1", "paper", "gmrf"):
+        reference_errors({key: out})
     print(json.dumps({"only": args.only, **out}), flush=True)
 
 
@@ -346,6 +360,15 @@ def run_ours(args, rank, world):
     latency = None
     if not args.no_latency and args.d is None:
         latency = latency_leg(args, torch)
+    config1 = None
+    if not args.no_config1 and args.d is None:
+        config1 = config1_leg(args, torch)
+    paper = None
+    if not args.no_paper and args.d is None:
+        paper = paper_leg(args, torch)
+    gmrf = None
+    if not args.no_gmrf and args.d is None:
+        gmrf = gmrf_leg(args, torch)
 
     if rank != 0:
         return
@@ -383,34 +406,46 @@ def run_ours(args, rank, world):
         line["dense"] = dense
     if latency is not None:
         line["latency"] = latency
+    if config1 is not None:
+        line["gmrf_config1"] = config1
+    if paper is not None:
+        line["paper"] = paper
+    if gmrf is not None:
+        line["gmrf"] = gmrf
     if not args.no_cpu_baseline:
         # the oracle on the original FP64 values, probe 0: the CPU baseline and
         # the reference for the relative errors of the FP32 and BF16 results
-        a_c, b_c = (interval if interval is not None else (a_e, b_e))
+        import oracle
+
+        # the oracle takes its own interval (closed form, or its Gershgorin pass)
+        a_c, b_c = interval if interval is not None else oracle.gershgorin(B.rowptr, B.col, B.val)
         dt, steps, probes, t_cpu, threads = cpu_sample(B, B.val, a_c, b_c, n, M, budget_s=args.cpu_budget)
         bg1, _, _ = algorithmic_bytes_per_step(B, 1, s_v)
         line["cpu_baseline"] = {"value": steps * bg1 / dt / 1e9, "unit": "GB/s", "cores": threads,
                                 "kind": "oracle",
                                 "sample": "probe 0 of %d, %d of %d degree steps, full d=%d, FP64" % (M, steps, n, B.d)}
         if t_cpu is not None:
-            import oracle
-
             gp0 = float(np.dot(oracle.cheb_coeffs(n, a_c, b_c), t_cpu[:, 0]))
             line["rel_err_probe0_vs_fp64_oracle"] = abs(gp0_ours - gp0) / abs(gp0)
             if bf16 is not None:
                 bf16["rel_err_probe0_vs_fp64_oracle"] = abs(bf16["gamma_p0"] - gp0) / abs(gp0)
+        reference_errors(line)
     print(json.dumps(line), flush=True)
 
 
-def _forward_and_grad(K, n, M, a, b, steps, torch, checkpoint_too):
-    """CUDA-event times of cld_estimate and cld_grad on one matrix (autotuned),
-    and optionally of the checkpointed cld_grad."""
+def _forward_and_grad(K, n, M, a, b, steps, torch, checkpoint_too, variant=None):
+    """CUDA-event times of cld_estimate and cld_grad on one matrix (autotuned
+    unless ``variant`` pins the inner loop), and optionally of the
+    checkpointed cld_grad."""
     from paper_1503_06394_gb300 import CsrLogdet
 
     v32, _ = K.stored("f32")
     m = CsrLogdet(K.rowptr, K.col, v32)
     m.set_interval(a, b)
-    variant, _ = m.autotune(n, M)
+    if variant is None:
+        variant, _ = m.autotune(n, M)
+    else:
+        m.set_kernel_variant(variant)
     ws_all = m.reserve(n, M, 1)
     m.estimate(n, M, 0)
     m.grad(n, M, 0)
@@ -474,7 +509,7 @@ def adjoint_leg(args, torch, world):
         _, v64 = K.stored("f32")
         a = cfg["sigma2"]
         b = float(np.max(np.add.reduceat(np.abs(v64), K.rowptr[:-1])))
-        res[order] = _forward_and_grad(K, n, M, a, b, steps, torch, order == "cell")
+        res[order] = _forward_and_grad(K, n, M, a, b, steps, torch, order == "cell", args.variant)
         res[order]["interval"] = [a, b]
         nnz, d = K.nnz, K.d
         del K
@@ -496,65 +531,103 @@ def adjoint_leg(args, torch, world):
 
 
 def batch_bytes(mats, M, s_v, general):
-    """Algorithmic bytes of one degree step over all blocks (no gather reuse)."""
-    tot = 0
+    """Algorithmic bytes of one degree step over all blocks: (B_gather, B_min).
+
+    SPD blocks: one pass reads the CSR, w_j and w_{j-1} and writes w_{j+1}:
+    B_min = csr + 3 d M 4; B_gather adds one M-wide row of w_j per stored
+    off-diagonal entry.  General blocks (Algorithm 2): a first pass y = C w_j
+    reads C's CSR and w_j and writes y; a second applies C^T to y with the
+    recurrence, reading C^T's CSR, y, w_j and w_{j-1} and writing w_{j+1}:
+    B_min = 2 csr + 6 d M 4 (y spans all blocks, far more than L2, so it
+    goes to DRAM and back); B_gather adds the gathered rows of both passes."""
+    bg = bm = 0
     for m in mats:
         rows = np.repeat(np.arange(m.d), np.diff(m.rowptr))
         off = int(np.count_nonzero(m.col != rows))
         csr = m.nnz * (s_v + 4) + 8 * (m.d + 1)
-        if general:  # y = C w_j (gather w_j, write y), then C^T y (gather y, own, prev, write)
-            tot += 2 * csr + 2 * off * M * 4 + 4 * m.d * M * 4
+        if general:
+            bm += 2 * csr + 6 * m.d * M * 4
+            bg += 2 * csr + 2 * off * M * 4 + 6 * m.d * M * 4
         else:
-            tot += csr + off * M * 4 + 3 * m.d * M * 4
-    return tot
+            bm += csr + 3 * m.d * M * 4
+            bg += csr + off * M * 4 + 3 * m.d * M * 4
+    return bg, bm
 
 
 def batch_leg(args, torch):
     """Config 4: 512 matrices, d log-uniform in [1e3, 2e5]; the SPD half and the
     general half (1/2 logdet C^T C) each in one batched estimate replayed as a
-    CUDA graph, against a loop of single-matrix estimates on the same GPU."""
+    CUDA graph, against a loop of single-matrix estimates on the same GPU.
+    Each arm is timed as `reps` separately timed estimates (CUDA events);
+    the median is reported with the spread.  The roofline of the batched step
+    kernel is its mean launch time (profiled estimate) against B_min: every
+    block's w_j is at most 12.8 MB, so gathers are L2 hits and the DRAM
+    traffic a launch must move is the CSR plus the recurrence blocks."""
     from paper_1503_06394_gb300 import CsrBatchLogdet, CsrLogdet
 
     cfg = workloads.CONFIGS[4]
     n, M = cfg["n"], cfg["M"]
     spd, gen = workloads.batch_mixed(cfg["count"], cfg["dmin"], cfg["dmax"], cfg["seed"])
+    peak, src = read_peaks()
     out = {"workload": "%d matrices, d log-uniform in [%g, %g] (sum d = %d), half SPD, half general; n=%d, M=%d" % (
         cfg["count"], cfg["dmin"], cfg["dmax"], sum(m.d for m in spd + gen), n, M),
-           "gbs_model": "B_gather per block (no reuse); every block's w_j (<= 12.8 MB) fits in L2, so "
-                        "gathers mostly hit L2 and this effective rate can exceed the DRAM copy peak"}
-    steps = max(1, args.steps)
+           "bytes_model": "B_min per degree step: SPD csr + 3 d M 4, general 2 csr + 6 d M 4 (see batch_bytes)",
+           "peak_gbs": peak, "peak_source": src}
+    reps = max(7, args.steps)
     for dtype in ("f32", "bf16"):
-        tot_ms, tot_bytes = 0.0, 0
+        tot_ms, tot_bmin = 0.0, 0
         for kind, mats in (("spd", spd), ("general", gen)):
             br, S = workloads.block_diag(mats)
             st, _ = S.stored(dtype)
             bt = CsrBatchLogdet(br, S.rowptr, S.col, st, dtype=dtype, kind=kind)
             bt.auto_intervals()
-            v, _ = bt.autotune(n, M)
+            if args.variant is None:
+                v, _ = bt.autotune(n, M)
+            else:  # pinned (profiling captures): no autotuner launches
+                v = args.variant
+                bt.set_kernel_variant(v)
+                if args.tile_rows:
+                    bt.set_tile_rows(args.tile_rows)
             tile_rows = bt.tile_rows
-            bt.set_graph(True)
             bt.reserve(n, M)
-            for _ in range(2):
+            # the step kernel alone: plain launches with profiling events
+            bt.set_graph(False)
+            bt.set_profiling(True)
+            bt.estimate(n, M, 0)
+            kms, klaunch, _ = bt.last_timing()
+            bt.set_profiling(False)
+            bt.set_graph(True)
+            for _ in range(3):
                 bt.estimate(n, M, 0)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
             torch.cuda.synchronize()
-            e0.record()
-            for _ in range(steps):
-                r = bt.estimate(n, M, 0)
-            e1.record()
+            for e0, e1 in ev:
+                e0.record()
+                bt.estimate(n, M, 0)
+                e1.record()
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+            each = sorted(e0.elapsed_time(e1) for e0, e1 in ev)
+            ms = float(np.median(each))
             bt.close()
             del bt
-            nbytes = n * batch_bytes(mats, M, 2 if dtype == "bf16" else 4, kind == "general")
-            out["%s_%s_ms" % (kind, dtype)] = ms
-            out["%s_%s_gbs" % (kind, dtype)] = nbytes / (ms / 1e3) / 1e9
-            out["%s_%s_variant" % (kind, dtype)] = v
-            out["%s_%s_tile_rows" % (kind, dtype)] = tile_rows
+            s_v = 2 if dtype == "bf16" else 4
+            bg, bm = batch_bytes(mats, M, s_v, kind == "general")
+            # mean time of one general degree step (both passes for general blocks)
+            kernel_ms = kms / max(1, klaunch)
+            key = "%s_%s" % (kind, dtype)
+            out[key + "_ms"] = ms
+            out[key + "_ms_min_max"] = [each[0], each[-1]]
+            out[key + "_gbs_bmin"] = n * bm / (ms / 1e3) / 1e9
+            out[key + "_gbs_gather"] = n * bg / (ms / 1e3) / 1e9
+            out[key + "_step_kernel_ms"] = kernel_ms
+            out[key + "_step_frac_bmin"] = bm / (kernel_ms / 1e3) / 1e9 / peak
+            out[key + "_variant"] = v
+            out[key + "_tile_rows"] = tile_rows
             tot_ms += ms
-            tot_bytes += nbytes
+            tot_bmin += n * bm
         out["batched_%s_ms" % dtype] = tot_ms
-        out["batched_%s_gbs" % dtype] = tot_bytes / (tot_ms / 1e3) / 1e9
+        out["batched_%s_gbs_bmin" % dtype] = tot_bmin / (tot_ms / 1e3) / 1e9
+        out["batched_%s_frac_bmin" % dtype] = tot_bmin / (tot_ms / 1e3) / 1e9 / peak
     # per-matrix loop (FP32): one handle per matrix, estimates one after another
     handles = []
     for kind, mats in (("spd", spd), ("general", gen)):
@@ -588,8 +661,9 @@ def gmrf_leg(args, torch):
     correlation rho = -0.22, drawn by a chequerboard Gibbs sampler
     (x_i | rest ~ N(rho * sum of neighbours, 1)); then the log-likelihood
     1/2 logdet J(rho) - 1/2 x^T J(rho) x over a grid of rho, logdet J(rho)
-    estimated on the GPU (n = 60, M = 16) and, for comparison, exact from the
-    separable spectrum 1 - rho (2 cos(pi i/(N+1)) + 2 cos(pi j/(N+1)))."""
+    estimated on the GPU (n = 60, M = 16).  The exact logdet from the
+    separable spectrum 1 - rho (2 cos(pi i/(N+1)) + 2 cos(pi j/(N+1))) and
+    the argmax it gives are added by the CPU-baseline block."""
     from paper_1503_06394_gb300 import CsrLogdet
 
     N = int(round((args.d or 25_000_000) ** 0.5))
@@ -598,6 +672,7 @@ def gmrf_leg(args, torch):
     x = torch.zeros((N + 2, N + 2), dtype=torch.float64, device="cuda")  # zero halo
     ii, jj = torch.meshgrid(torch.arange(N, device="cuda"), torch.arange(N, device="cuda"), indexing="ij")
     colour = ((ii + jj) % 2).bool()
+    torch.cuda.synchronize()
     t0 = time.time()
     for _ in range(sweeps):
         for c in (False, True):
@@ -609,56 +684,63 @@ def gmrf_leg(args, torch):
     sum_sq = float((xs * xs).sum())
     xax = float(2 * ((xs[:-1, :] * xs[1:, :]).sum() + (xs[:, :-1] * xs[:, 1:]).sum()))  # x^T A x
     gibbs_s = time.time() - t0
-    del x, ii, jj, colour
-    J = workloads.gmrf_grid(N, 0.0)
-    rows = np.repeat(np.arange(J.d), np.diff(J.rowptr))
-    diag = torch.as_tensor(J.col == rows, device="cuda")
-    vals = torch.ones(J.nnz, dtype=torch.float32, device="cuda")
-    m = CsrLogdet(J.rowptr, J.col, vals)
+    del x, ii, jj, colour, xs
+    rowptr, col, diag = workloads.grid_pattern_device(N, torch)
+    vals = torch.ones(col.shape[0], dtype=torch.float32, device="cuda")
+    m = CsrLogdet(rowptr, col, vals)
     n, M = 60, 16
-    c = np.cos(np.pi * np.arange(1, N + 1) / (N + 1))
     sweep = []
+    torch.cuda.synchronize()
     t0 = time.time()
     for rho in np.round(np.arange(-0.245, 0.0001, 0.005), 4):
         m.val.copy_(torch.where(diag, 1.0, float(rho)).float())  # values of J(rho), same pattern
         m.set_interval(1 - 4 * abs(rho) - 1e-6, 1 + 4 * abs(rho) + 1e-6)
         r = m.estimate(n, M, 0)
-        mu = 1.0 - rho * 2.0 * (c[:, None] + c[None, :])
-        exact = float(np.sum(np.log(mu)))
         quad = sum_sq - rho * xax
-        sweep.append({"rho": float(rho), "logdet": r["logdet"], "stderr": r["stderr"], "logdet_exact": exact,
-                      "loglik": 0.5 * r["logdet"] - 0.5 * quad, "loglik_exact": 0.5 * exact - 0.5 * quad})
+        sweep.append({"rho": float(rho), "logdet": r["logdet"], "stderr": r["stderr"],
+                      "loglik": 0.5 * r["logdet"] - 0.5 * quad, "quad": quad})
     sweep_s = time.time() - t0
+    nnz = int(col.shape[0])
     m.close()
+    del m, rowptr, col, diag, vals
+    torch.cuda.empty_cache()
     best = max(sweep, key=lambda e: e["loglik"])
-    best_exact = max(sweep, key=lambda e: e["loglik_exact"])
     return {"workload": "GMRF grid %d x %d (d=%d, nnz=%d), Gibbs sample at rho=%g (%d sweeps), n=%d, M=%d" % (
-                N, N, J.d, J.nnz, rho0, sweeps, n, M),
-            "argmax_rho": best["rho"], "argmax_rho_exact_logdet": best_exact["rho"], "true_rho": rho0,
-            "gibbs_s": gibbs_s, "sweep_s": sweep_s, "estimates": len(sweep),
-            "max_rel_err_logdet": max(abs(e["logdet"] - e["logdet_exact"]) / abs(e["logdet_exact"])
-                                      for e in sweep if e["logdet_exact"] != 0),
-            "sweep": sweep}
+                N, N, N * N, nnz, rho0, sweeps, n, M),
+            "N": N, "argmax_rho": best["rho"], "true_rho": rho0,
+            "gibbs_s": gibbs_s, "sweep_s": sweep_s, "estimates": len(sweep), "sweep": sweep}
 
 
 def paper_leg(args, torch):
     """The paper's timing experiment (Sec. 5.1, Fig. 1a): Algorithm 2 on its own
     sparse random generator (five U[-1,1] off-diagonals per row, mirrored,
     diagonal = absolute row sum + 1e-3) with m = 10, n = 15,
-    sigma_min = 1e-3, sigma_max = ||C||_1, at d = 3e7 (about 3e8 stored
-    entries).  The paper reports 500 s on a 3.40 GHz Intel i7.  Accuracy point:
-    the same setting at d = 1e4 against numpy's log|det C|."""
+    sigma_min = 1e-3, sigma_max = ||C||_1, at d = 3e7 (about 3.3e8 stored
+    entries, built on the device).  The paper reports 500 s on a 3.40 GHz
+    Intel i7.  Accuracy point: the same setting at d = 1e4 (numpy generator);
+    its error against numpy's log|det C| is added by the CPU-baseline block."""
     from paper_1503_06394_gb300 import CsrLogdet
 
     n, M = 15, 10
-    out = {"paper_seconds": 500.0, "paper_hardware": "3.40 GHz Intel i7, 24 GB RAM (Sec. 5.1)"}
+    out = {"paper_seconds": 500.0, "paper_hardware": "3.40 GHz Intel i7, 24 GB RAM (Sec. 5.1)", "n": n, "m": M}
     for d in (10_000, args.d or 30_000_000):
         t0 = time.time()
-        C = workloads.paper_sparse_random(d, 1006)
+        if d <= 20000:
+            C = workloads.paper_sparse_random(d, 1006)
+            rowptr, col = C.rowptr, C.col
+            v32, v64 = C.stored("f32")
+            smax = float(np.max(np.add.reduceat(np.abs(v64), C.rowptr[:-1])))  # ||C||_1 = ||C||_inf
+            nnz = C.nnz
+        else:
+            rowptr, col, v64 = workloads.paper_sparse_random_device(d, 1006, torch)
+            v32 = v64.float()
+            rows = torch.repeat_interleave(torch.arange(d, device="cuda"), torch.diff(rowptr))
+            smax = float(torch.zeros(d, dtype=torch.float64, device="cuda").index_add_(0, rows, v32.double().abs()).max())
+            nnz = int(col.shape[0])
+            del v64, rows
+        torch.cuda.synchronize()
         gen = time.time() - t0
-        v32, v64 = C.stored("f32")
-        smax = float(np.max(np.add.reduceat(np.abs(v64), C.rowptr[:-1])))  # ||C||_1 = ||C||_inf (symmetric)
-        m = CsrLogdet(C.rowptr, C.col, v32, kind="general")
+        m = CsrLogdet(rowptr, col, v32, kind="general")
         m.set_interval(1e-6, smax ** 2)
         m.reserve(n, M)
         m.estimate(n, M, 0)
@@ -670,34 +752,63 @@ def paper_leg(args, torch):
         torch.cuda.synchronize()
         sec = (time.perf_counter() - t0) / reps
         m.close()
-        key = "d%d" % d
-        out[key] = {"nnz": C.nnz, "seconds": sec, "logdet": r["logdet"], "stderr": r["stderr"],
-                    "speedup_vs_paper": (500.0 / sec) if d >= 30_000_000 else None, "generation_s": gen}
-        if d <= 20000:
-            exact = float(np.linalg.slogdet(C.dense())[1])
-            out[key]["exact"] = exact
-            out[key]["rel_err"] = abs(r["logdet"] - exact) / abs(exact)
-        del C, v32, v64
+        del m, rowptr, col, v32
         torch.cuda.empty_cache()
+        out["d%d" % d] = {"nnz": nnz, "seconds": sec, "logdet": r["logdet"], "stderr": r["stderr"],
+                          "speedup_vs_paper": (500.0 / sec) if d >= 30_000_000 else None, "generation_s": gen,
+                          "generator": "numpy (workloads.paper_sparse_random)" if d <= 20000 else
+                          "device (workloads.paper_sparse_random_device)"}
     return out
+
+
+def config1_leg(args, torch):
+    """Config 1: the GMRF precision 0.1 I + L on a 1000 x 1000 grid (d = 1e6,
+    5-point Dirichlet Laplacian, nnz = 4,996,000), FP32, n = 50, M = 64, the
+    closed-form interval [0.1, 8.1].  Whole-estimate time (CUDA events) and the
+    general step kernel's mean launch time against B_min: the stencil's
+    neighbour rows are L2 hits, so each step must move the CSR once and
+    w_{j-1}, w_j, w_{j+1} once."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    cfg = workloads.CONFIGS[1]
+    B = workloads.make(cfg)
+    v32, _ = B.stored("f32")
+    n, M = cfg["n"], cfg["M"]
+    interval = (cfg["kappa2"], cfg["kappa2"] + 8.0)
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    m.set_interval(*interval)
+    variant, _ = m.autotune(n, M)
+    m.reserve(n, M)
+    ms, kernel_ms, launches, _, r = time_estimates(m, n, M, cfg["probe_seed"], interval, max(3, args.steps),
+                                                  max(3, args.warmup), torch, 1)
+    m.close()
+    del m
+    torch.cuda.empty_cache()
+    _, bmin, _ = algorithmic_bytes_per_step(B, M, 4)
+    peak, src = read_peaks()
+    return {"workload": "grid_gmrf N=%d (d=%d, nnz=%d) kappa2=%g, FP32, n=%d, M=%d, interval %s" % (
+                cfg["N"], B.d, B.nnz, cfg["kappa2"], n, M, list(interval)),
+            "ms_per_estimate": ms, "variant": variant, "step_kernel_ms": kernel_ms,
+            "b_min_per_step": bmin, "step_gbs_bmin": bmin / (kernel_ms / 1e3) / 1e9,
+            "step_frac_bmin": bmin / (kernel_ms / 1e3) / 1e9 / peak, "peak_gbs": peak, "peak_source": src,
+            "estimate_gbs_bmin": n * bmin / (ms / 1e3) / 1e9, "logdet": r["logdet"], "stderr": r["stderr"]}
 
 
 def latency_leg(args, torch):
     """Config 0 (d = 2048, n = 30, M = 30): a launch- and latency-bound size.
     Time per estimate with plain launches and with the whole estimate replayed
-    as one CUDA graph; errors against the oracle (same probes) and against the
-    exact Cholesky value."""
-    import oracle
+    as one CUDA graph, the interval from the device's own Gershgorin pass.  The
+    errors against the oracle (same probes) and the exact Cholesky value are
+    added by the CPU-baseline block (``reference_errors``)."""
     from paper_1503_06394_gb300 import CsrLogdet
 
     cfg = workloads.CONFIGS[0]
     B = workloads.make(cfg)
-    v32, v64 = B.stored("f32")
+    v32, _ = B.stored("f32")
     n, M = cfg["n"], cfg["M"]
-    a, b = oracle.gershgorin(B.rowptr, B.col, v64)
     m = CsrLogdet(B.rowptr, B.col, v32)
-    m.set_interval(a, b)
     m.reserve(n, M)
+    a_gpu, b_gpu = m.auto_interval(0)  # the device's own Gershgorin pass
     out = {"workload": "sparse_random_spd d=%d picks=%d seed=%d, n=%d, M=%d" % (B.d, cfg["picks"], cfg["seed"], n, M)}
     reps = 50
     for mode in ("launches", "graph"):
@@ -710,13 +821,53 @@ def latency_leg(args, torch):
             r = m.estimate(n, M, cfg["probe_seed"])
         out["%s_us" % mode] = (time.perf_counter() - t0) / reps * 1e6
     m.close()
-    ref = oracle.estimate(B.rowptr, B.col, v64, a, b, n, M, seed=cfg["probe_seed"])
-    exact = oracle.logdet_cholesky(workloads.Csr(B.rowptr, B.col, v64).dense())
-    out.update({"logdet": r["logdet"], "stderr": r["stderr"], "exact_cholesky": exact,
-                "rel_err_vs_oracle": abs(r["logdet"] - ref["gamma"]) / abs(ref["gamma"]),
-                "rel_err_vs_exact": abs(r["logdet"] - exact) / abs(exact),
+    out.update({"interval": [a_gpu, b_gpu], "logdet": r["logdet"], "stderr": r["stderr"],
                 "timing": "host wall clock per estimate call (includes the result read-back)"})
     return out
+
+
+def reference_errors(line):
+    """Part of the CPU-baseline leg: the oracle's and the closed forms' values
+    for the small legs, and the GPU results' errors against them.  Runs after
+    every GPU measurement; no value here feeds a GPU call."""
+    import oracle
+
+    lat = line.get("latency")
+    if lat is not None:
+        cfg = workloads.CONFIGS[0]
+        B = workloads.make(cfg)
+        _, v64 = B.stored("f32")
+        a, b = oracle.gershgorin(B.rowptr, B.col, v64)  # the oracle's own interval
+        ref = oracle.estimate(B.rowptr, B.col, v64, a, b, cfg["n"], cfg["M"], seed=cfg["probe_seed"])
+        exact = oracle.logdet_cholesky(workloads.Csr(B.rowptr, B.col, v64).dense())
+        lat.update({"interval_rel_diff_vs_oracle": max(abs(lat["interval"][0] - a) / a, abs(lat["interval"][1] - b) / b),
+                    "oracle_logdet": ref["gamma"], "exact_cholesky": exact,
+                    "rel_err_vs_oracle": abs(lat["logdet"] - ref["gamma"]) / abs(ref["gamma"]),
+                    "rel_err_vs_exact": abs(lat["logdet"] - exact) / abs(exact)})
+    pl = line.get("paper")
+    if pl is not None and "d10000" in pl:
+        C = workloads.paper_sparse_random(10_000, 1006)
+        exact = float(np.linalg.slogdet(C.dense())[1])
+        pl["d10000"].update({"exact": exact, "rel_err": abs(pl["d10000"]["logdet"] - exact) / abs(exact)})
+    gm = line.get("gmrf")
+    if gm is not None:
+        N = gm["N"]
+        c = np.cos(np.pi * np.arange(1, N + 1) / (N + 1))
+        for e in gm["sweep"]:
+            exact = float(np.sum(np.log(1.0 - e["rho"] * 2.0 * (c[:, None] + c[None, :]))))
+            e["logdet_exact"] = exact
+            e["loglik_exact"] = 0.5 * exact - 0.5 * e["quad"]
+        gm["argmax_rho_exact_logdet"] = max(gm["sweep"], key=lambda e: e["loglik_exact"])["rho"]
+        gm["max_rel_err_logdet"] = max(abs(e["logdet"] - e["logdet_exact"]) / abs(e["logdet_exact"])
+                                       for e in gm["sweep"] if e["logdet_exact"] != 0)
+        gm["max_err_in_stderrs"] = max(abs(e["logdet"] - e["logdet_exact"]) / e["stderr"] for e in gm["sweep"]
+                                       if e["stderr"] > 0)
+    g1 = line.get("gmrf_config1")
+    if g1 is not None:
+        cfg = workloads.CONFIGS[1]
+        exact = oracle.grid_laplacian_logdet(cfg["N"], cfg["kappa2"])
+        g1.update({"exact_closed_form": exact, "rel_err_vs_exact": abs(g1["logdet"] - exact) / abs(exact),
+                   "err_in_stderrs": abs(g1["logdet"] - exact) / g1["stderr"]})
 
 
 def dense_leg(args, torch):
@@ -797,11 +948,17 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config 4) measurement")
     ap.add_argument("--no-dense", action="store_true", help="skip the dense tensor-core measurement")
     ap.add_argument("--no-latency", action="store_true", help="skip the config-0 latency measurement")
-    ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency", "gmrf"], default=None,
+    ap.add_argument("--no-config1", action="store_true", help="skip the config-1 (grid GMRF) measurement")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's Sec. 5.1 timing replay")
+    ap.add_argument("--no-gmrf", action="store_true", help="skip the paper's Sec. 5.2 GMRF likelihood sweep")
+    ap.add_argument("--only", choices=["dense", "adjoint", "paper", "latency", "gmrf", "config1", "batch"],
+                    default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
     ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
                     help="pin the recurrence-step inner-loop variant instead of autotuning it")
+    ap.add_argument("--tile-rows", type=int, default=None,
+                    help="with --variant and --only batch: rows per work tile of the batched step")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

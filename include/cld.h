@@ -75,7 +75,10 @@ typedef enum { CLD_SPD = 0, CLD_GENERAL = 1 } cld_kind;
 /* Largest probe count handled by one pass; larger M runs in panels of 128. */
 #define CLD_PROBE_PANEL 128
 
-/* Creates a handle for a d x d CSR matrix on the device.
+/* Creates a handle for a d x d CSR matrix on the device: the input B of
+ * Algorithm 1 (Sec. 3.1) or C of Algorithm 2 (Sec. 3.2), which the paper
+ * takes as a sparse matrix accessed only through products (Sec. 3.1: cost
+ * O(mn ||B||_0)); the storage format itself has no paper counterpart.
  *   rowptr: d+1 int64 (device), rowptr[0] = 0, non-decreasing, rowptr[d] = nnz
  *   col:    nnz int32 (device), 0 <= col < d
  *   val:    nnz values (device) of type val_dtype
@@ -105,10 +108,14 @@ CLD_API cld_status cld_create_dense(cld_handle* out, int64_t d, int64_t ld, cons
                                     cld_dtype val_dtype, cld_kind kind, void* stream);
 
 /* Bytes of device workspace an estimate of degree n with M probes needs
- * (with_grad != 0: also enough for cld_grad).  Errors: CLD_ERR_INVALID. */
+ * (with_grad != 0: also enough for cld_grad).  No paper counterpart
+ * (memory infrastructure): the three recurrence blocks w_{j-1}, w_j, w_{j+1}
+ * of Algorithm 1 are the dominant term, d x panel x 4 bytes each.
+ * Errors: CLD_ERR_INVALID. */
 CLD_API cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes);
 
-/* Attaches caller-owned device workspace (at least 256-byte aligned) and
+/* No paper counterpart (memory infrastructure).
+ * Attaches caller-owned device workspace (at least 256-byte aligned) and
  * validates the CSR arrays on the device (monotone rowptr, column range,
  * finite values).  The workspace must stay alive until cld_destroy or the
  * next cld_set_workspace.  Errors: CLD_ERR_INVALID (malformed CSR or
@@ -137,7 +144,12 @@ CLD_API cld_status cld_set_interval(cld_handle h, double a, double b);
  * CLD_ERR_INTERVAL, CLD_ERR_NOMEM, CLD_ERR_CUDA. */
 CLD_API cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a, double* b);
 
-/* Runs the estimator: degree n >= 0, M >= 1 probes, probe seed `seed`.
+/* Runs the estimator of Algorithm 1 (Sec. 3.1; CLD_SPD) or Algorithm 2
+ * (Sec. 3.2; CLD_GENERAL): Rademacher probes and the Hutchinson trace
+ * estimate of Sec. 2.2, the Chebyshev recurrence of Eq. (chebreq) applied to
+ * the probes, and the coefficients of the degree-n interpolant of log at the
+ * first-kind nodes of Sec. 2.1, on the interval set on the handle.
+ * Degree n >= 0, M >= 1 probes, probe seed `seed`.
  *   logdet_out: Gamma (CLD_SPD: logdet B; CLD_GENERAL: log|det C|)
  *   stderr_out: std over probes of Gamma_p divided by sqrt(M) (NULL ok;
  *               NaN when M = 1); for CLD_GENERAL it is halved as well
@@ -148,8 +160,9 @@ CLD_API cld_status cld_auto_interval(cld_handle h, int lanczos_iters, double* a,
 CLD_API cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
                         double* stderr_out, double* moments_out);
 
-/* After a successful cld_estimate: copies the n+1 coefficients c_j used and
- * the M per-probe estimates Gamma_p to host arrays (either may be NULL). */
+/* After a successful cld_estimate: copies the n+1 coefficients c_j used
+ * (Sec. 2.1) and the M per-probe estimates Gamma_p (the summands of the
+ * Hutchinson average of Algorithm 1) to host arrays (either may be NULL). */
 CLD_API cld_status cld_last_details(cld_handle h, double* coeffs_out, double* gamma_p_out);
 
 /* Gradient of the estimate (same n, M, seed and interval, interval held fixed)
@@ -163,7 +176,7 @@ CLD_API cld_status cld_last_details(cld_handle h, double* coeffs_out, double* ga
 CLD_API cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
                     float* dvalues_dev);
 
-/* Memory of cld_grad.  interval 0 (default): the forward keeps every w_1..w_n
+/* Memory of cld_grad (an extension; no paper counterpart).  interval 0 (default): the forward keeps every w_1..w_n
  * (n blocks of d x panel floats).  interval K >= 2: the forward keeps only the
  * pairs (w_{sK-1}, w_{sK}); the reverse pass recomputes w_{sK+1} .. w_{(s+1)K}
  * from them, segment by segment from the last, before taking those reverse
@@ -173,7 +186,8 @@ CLD_API cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* l
  * Errors: CLD_ERR_INVALID for 1, a negative value or more than 100000. */
 CLD_API cld_status cld_set_grad_checkpoint(cld_handle h, int interval);
 
-/* One-shot estimate from HOST arrays: copies the CSR (rowptr, col, val as
+/* One-shot estimate from HOST arrays (Algorithm 1 or 2 as cld_estimate; the
+ * copies are infrastructure without a paper counterpart): copies the CSR (rowptr, col, val as
  * above but in host memory, ideally pinned) into the front of the device
  * workspace, runs cld_estimate on [a, b] and returns Gamma and its stderr.
  * Workspace size: cld_host_workspace_size.  Nothing is kept after return.
@@ -209,8 +223,12 @@ CLD_API cld_status cld_logdet_csr_host(int64_t d, int64_t nnz, const int64_t* ro
  * requests that do not fit are rejected with CLD_ERR_NOMEM and a message that
  * gives both sizes.  No cudaMalloc, cudaFree or allocating library routine is
  * called.  The first call on each device looks up the array's device address
- * on that device (cudaGetSymbolAddress, with that device current); make that
- * first call before any stream capture.  All calls share the one array and it
+ * on that device (cudaGetSymbolAddress, with that device current) and keeps
+ * it for the life of the process; make that first call before any stream
+ * capture, and do not use the entry point across a cudaDeviceReset (or any
+ * other re-creation of the device's primary context), after which the kept
+ * address is stale.  Each CSR array must be aligned to its element size; a
+ * pointer that is not is refused with CLD_ERR_INVALID before any CUDA call.  All calls share the one array and it
  * keeps the last call's contents (the call clears what must start at zero):
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it.  Synchronises `stream` to return.  Errors: as cld_create_csr,
@@ -227,7 +245,8 @@ CLD_API cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t* ro
 /* of Algorithm 1, or of Algorithm 2 for CLD_GENERAL).                        */
 /* ------------------------------------------------------------------------ */
 
-/* Creates a batch handle.  The nb matrices are given as one block-diagonal
+/* Creates a batch handle (no paper counterpart: each block is an
+ * independent problem of Algorithm 1 or 2).  The nb matrices are given as one block-diagonal
  * CSR with GLOBAL row and column indices: block b holds rows (and columns)
  * [blk_rows[b], blk_rows[b+1]); blk_rows is a HOST array of nb+1 offsets,
  * copied.  rowptr/col/val/val_dtype/kind/stream as in cld_create_csr (all
@@ -240,34 +259,37 @@ CLD_API cld_status cld_create_batch(cld_handle* out, int nb, const int64_t* blk_
                                     const int64_t* rowptr, const int32_t* col, const void* val,
                                     cld_dtype val_dtype, cld_kind kind, void* stream);
 
-/* Rows per work tile of the batched step kernel (>= 256; default 1024): a
+/* Tuning control, no paper counterpart.  Rows per work tile of the batched step kernel (>= 256; default 1024): a
  * tile never spans two blocks; CTAs take tiles from a static queue.
  * cld_autotune on a batch handle also picks it (256 ... 4096). */
 CLD_API cld_status cld_batch_set_tile_rows(cld_handle h, int rows);
 
-/* The current rows per tile of a batch handle.  Errors: CLD_ERR_INVALID. */
+/* The current rows per tile of a batch handle (no paper counterpart).  Errors: CLD_ERR_INVALID. */
 CLD_API cld_status cld_batch_get_tile_rows(cld_handle h, int* rows);
 
-/* Per-block intervals (host arrays of nb doubles), as cld_set_interval. */
+/* Per-block intervals (host arrays of nb doubles), as cld_set_interval (Sec. 3). */
 CLD_API cld_status cld_batch_set_intervals(cld_handle h, const double* a, const double* b);
 
-/* Per-block intervals computed on the device as cld_auto_interval (without
+/* Per-block intervals computed on the device as cld_auto_interval (Sec. 3.2; without
  * Lanczos); written to the host arrays a_out, b_out (nb each, may be NULL). */
 CLD_API cld_status cld_batch_auto_intervals(cld_handle h, double* a_out, double* b_out);
 
-/* Runs all blocks: logdet_out[b] and stderr_out[b] (host arrays of nb; the
+/* Runs all blocks, each as cld_estimate (Algorithm 1 or 2): logdet_out[b] and stderr_out[b] (host arrays of nb; the
  * latter may be NULL).  Errors as cld_estimate (CLD_ERR_SPECTRUM names the
  * first failing block; all outputs are still written). */
 CLD_API cld_status cld_batch_estimate(cld_handle h, int n, int M, uint64_t seed, double* logdet_out,
                                       double* stderr_out);
 
-/* When on, cld_estimate / cld_batch_estimate replay one CUDA graph of the
+/* Execution control, no paper counterpart.  When on, cld_estimate /
+ * cld_batch_estimate replay one CUDA graph of the
  * whole estimate (captured on first use per (n, M, variant, workspace, tile
  * size) on a stream of the handle; the seed is set by a launch before it).
  * Profiling events are not recorded in graph mode. */
 CLD_API cld_status cld_set_graph(cld_handle h, int on);
 
-/* Selects the inner loop of the recurrence-step kernel (a tuning control; all
+/* Selects the inner loop of the recurrence-step kernel (the matrix-block
+ * product of the recurrence in Algorithm 1; a tuning control with no paper
+ * counterpart; all
  * variants compute the same sums in the same order):
  *   0: each lane loads 4 (column, value) pairs itself, 4 row gathers in flight;
  *   1: the lanes of a row load 8 pairs cooperatively and issue 8 row gathers
@@ -292,29 +314,37 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  * Errors: CLD_ERR_INVALID for an unknown variant. */
 CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
 
-/* Autotuner: times `reps` launches of the general recurrence step of every
- * variant on this matrix with M probes (workspace and interval must be set;
+/* Autotuner (no paper counterpart): times three blocks of `reps` launches of
+ * the general recurrence step of every variant on this matrix with M probes,
+ * each candidate scored by its fastest block (workspace and interval must be set;
  * the workspace contents are overwritten) and keeps the fastest on the handle
  * (the current choice stays unless another is at least 2 % faster).  On a
  * batch handle every variant is timed at every tile size of 256, 512, 1024,
  * 2048 and 4096 rows and the fastest pair is kept (read the tile size back
  * with cld_batch_get_tile_rows).
- * Returns the chosen variant and its mean step time in ms (either may be NULL).
+ * Returns the chosen variant and its step time in ms (either may be NULL).
  * Errors: CLD_ERR_INVALID, CLD_ERR_NOMEM, CLD_ERR_INTERVAL, CLD_ERR_CUDA. */
 CLD_API cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* ms_out);
 
-/* Timing of the dominant kernel.  When on, every cld_estimate records CUDA
+/* Timing of the dominant kernel (no paper counterpart).  When on, every
+ * cld_estimate, and every cld_batch_estimate outside graph mode, records CUDA
  * events on its stream around the general recurrence steps (j >= 2) and
- * cld_last_timing returns their elapsed time and the number of such launches
- * in the last estimate.  Off by default. */
+ * cld_last_timing returns their elapsed time and the number of such degree
+ * steps in the last estimate (for CLD_GENERAL a degree step is two launches,
+ * C w_j then C^T y).  Off by default. */
 CLD_API cld_status cld_set_profiling(cld_handle h, int on);
 CLD_API cld_status cld_last_timing(cld_handle h, float* step_ms, int* step_launches, int* total_launches);
 
-/* Kernel configuration of the recurrence step, for reports: probe panel width
+/* Kernel configuration of the recurrence step, for reports (no paper
+ * counterpart): probe panel width
  * (padded M), lanes per row, CTAs per launch, threads per CTA. */
 CLD_API cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row, int* ctas,
                              int* threads);
 
+/* Handle and error infrastructure (no paper counterpart): cld_destroy frees
+ * the handle's host state and CUDA graph (never the borrowed arrays or the
+ * workspace); cld_last_error returns the calling thread's message for its
+ * last failed call; cld_version names the build. */
 CLD_API void cld_destroy(cld_handle h);
 CLD_API const char* cld_last_error(void);
 CLD_API const char* cld_version(void);

@@ -12,8 +12,8 @@ exact references that are easiest to state in numpy:
 * ``grid_laplacian_logdet`` -- log det(kappa^2 I + L) for the 5-point Dirichlet
   Laplacian on an N x N grid, from its separable eigenvalues
   kappa^2 + 4 sin^2(pi i / (2(N+1))) + 4 sin^2(pi j / (2(N+1))).
-* ``thm1_degree`` / ``thm1_samples`` -- the sufficient degree and sample count of
-  Theorem 1, and ``chebyshev_error_bound`` -- the per-eigenvalue bound
+* ``thm1_degree`` -- the sufficient degree of Theorem 1, and
+  ``chebyshev_error_bound`` -- the per-eigenvalue bound
   20 log(2(1/delta - 1)) / ((K-1) K^n) of Sec. 4.1.
 
 Every arithmetic function here is pinned by a CPU test against something other
@@ -297,7 +297,3 @@ def thm1_degree(delta: float, eps: float) -> float:
                  * np.log(2.0 * (1.0 / delta - 1.0)) / np.log(1.0 / (1.0 - delta)))
     return float(num / np.log(K))
 
-
-def thm1_samples(eps: float, zeta: float) -> float:
-    """Right-hand side of Theorem 1's condition on m: 54 eps^-2 log(2/zeta)."""
-    return float(54.0 / eps ** 2 * np.log(2.0 / zeta))

@@ -81,6 +81,12 @@ extern "C" cld_status cld_estimate_static(int64_t d, int64_t nnz, const int64_t*
     if (!rowptr || (nnz > 0 && (!col || !val))) return err(CLD_ERR_INVALID, "NULL CSR array");
     if (val_dtype != CLD_F32 && val_dtype != CLD_BF16 && val_dtype != CLD_F64)
         return err(CLD_ERR_INVALID, "unknown value dtype %d", (int)val_dtype);
+    // The kernels load each array at its element width: a pointer that is not
+    // aligned to it would fault on the device, so it is refused here, before
+    // any CUDA call.
+    const uintptr_t vsize = val_dtype == CLD_F32 ? 4 : val_dtype == CLD_BF16 ? 2 : 8;
+    if (((uintptr_t)rowptr) % 8 || ((uintptr_t)col) % 4 || ((uintptr_t)val) % vsize)
+        return err(CLD_ERR_INVALID, "CSR arrays must be aligned to their element size");
     if (n < 0 || M < 1 || n > 100000) return err(CLD_ERR_INVALID, "need 0 <= n <= 100000 and M >= 1");
     if (!(a > 0.0) || !(a < b) || !isfinite(a) || !isfinite(b))
         return err(CLD_ERR_INTERVAL, "interval must satisfy 0 < a < b (got [%g, %g])", a, b);

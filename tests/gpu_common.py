@@ -13,7 +13,15 @@ def require_gpu():
     return torch
 
 
-def moment_tol(d, n, structured=False, row_terms=16):
+def rows_per_lane(m, M):
+    """Rows one lane of the handle's step kernel visits (grid-stride), from its
+    launch configuration: the length of the lane's FP32 moment sum."""
+    _, lpr, ctas, threads = m.launch_config(M)
+    groups = max(1, ctas * threads // max(1, lpr))
+    return max(1, -(-m.d // groups))
+
+
+def moment_tol(d, n, structured=False, row_terms=16, rows_per_lane=1):
     """|t_gpu - t_oracle| bound for FP32 recurrence vectors against the FP64 oracle.
 
     Each step rounds w_{j+1} entries to FP32 (relative 2^-24 of terms bounded
@@ -26,13 +34,22 @@ def moment_tol(d, n, structured=False, row_terms=16):
     that many terms, whose random rounding grows like sqrt(terms); the bound
     scales by sqrt(row_terms / 16) beyond 16 (dense rows: row_terms = d).
 
+    ``rows_per_lane``: each lane sums v_i w_j[i] over the L rows it visits in
+    FP32 before the FP64 reduction.  With |w_j|_1 <= sqrt(d) |w_j|_2 <= d
+    (T_j(At) has spectral norm <= 1 on an enclosing interval) the terms have
+    mean magnitude at most 1; a sum of L such terms that share a sign (as
+    v_i w_1[i] ~ At_ii does) carries a rounding error of about
+    eps32 L^1.5 / sqrt(3), and the d / L lane sums add these at random, so the
+    total is about eps32 L sqrt(d) / sqrt(3).  The bound allows 8 eps32 L sqrt(d).
+
     ``structured=True`` drops the random-sign assumption: on matrices with a
     few distinct exactly-representable values (the grid Laplacian) the
     entries of w_j take few distinct values and their FP32 roundings share a
     sign, so the errors add up linearly: (j+1)^2 eps32 d."""
     eps = 2.0 ** -24
     j = np.arange(n + 1)[:, None]
+    acc = 8.0 * eps * rows_per_lane * np.sqrt(max(d, 1)) if rows_per_lane > 1 else 0.0
     if structured:
-        return (j + 1) ** 2 * eps * max(d, 1) + 1e-9 * max(d, 1)
+        return (j + 1) ** 2 * eps * max(d, 1) + 1e-9 * max(d, 1) + acc
     grow = np.sqrt(max(1.0, row_terms / 16.0))
-    return 64.0 * (j + 1) ** 2 * eps * np.sqrt(max(d, 1)) * grow + 1e-9 * max(d, 1)
+    return 64.0 * (j + 1) ** 2 * eps * np.sqrt(max(d, 1)) * grow + 1e-9 * max(d, 1) + acc

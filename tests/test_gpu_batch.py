@@ -277,3 +277,29 @@ def test_batch_rejects_off_block_columns(torch):
         bt.reserve(5, 4)
     assert e.value.status == Bd.CLD_ERR_INVALID
     bt.close()
+
+
+@pytest.mark.parametrize("kind", ["spd", "general"])
+def test_batch_profiling_counts_steps(torch, kind):
+    """Profiling events bracket the general degree steps of a batched estimate
+    with plain launches (not in graph mode); the results are unchanged."""
+    from paper_1503_06394_gb300 import CsrBatchLogdet
+
+    mats = spd_mats([300, 4000, 1025], 70) if kind == "spd" else \
+        [workloads.nonsymmetric_dominant(d, 3, 70 + i) for i, d in enumerate([300, 4000, 1025])]
+    br, S = workloads.block_diag(mats)
+    s32, _ = S.stored("f32")
+    a, b = intervals(mats, general=kind == "general")
+    bt = CsrBatchLogdet(br, S.rowptr, S.col, s32, kind=kind)
+    bt.set_intervals(a, b)
+    plain = bt.estimate(20, 16, 3)
+    bt.set_profiling(True)
+    prof = bt.estimate(20, 16, 3)
+    ms, steps, total = bt.last_timing()
+    assert ms > 0 and steps == 18 and total > steps
+    assert np.array_equal(plain["logdet"], prof["logdet"])
+    bt.set_graph(True)
+    bt.estimate(20, 16, 3)
+    ms, steps, _ = bt.last_timing()
+    assert ms == 0 and steps == 0
+    bt.close()

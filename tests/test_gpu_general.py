@@ -105,3 +105,62 @@ def test_spanning_trees_apex_graph(torch, nv, edges):
     m.close()
     for r in (rg, rs):
         assert abs(r["logdet"] - exact) <= 5 * r["stderr"] + 1e-3 * abs(exact), (r, exact)
+
+
+def test_paper_generator_alg2_matches_oracle(torch):
+    """The paper's own timing setting (Sec. 5.1) at d = 1e4: its sparse random
+    generator (five U[-1,1] picks per row, mirrored, diagonal = absolute row
+    sum + 1e-3), Algorithm 2 with sigma_min = 1e-3 and sigma_max = ||C||_1,
+    n = 15, m = 10.  Every moment against the oracle on the same probes, the
+    estimate within 1e-5 of the oracle and of the literal Algorithm 2; the
+    error against numpy's log|det C| is printed (n = 15 is the paper's low
+    degree, so that error is the method's, not the kernel's)."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    d, n, M = 10_000, 15, 10
+    C = workloads.paper_sparse_random(d, 1006)
+    c32, c64 = C.stored("f32")
+    smax = float(np.max(np.add.reduceat(np.abs(c64), C.rowptr[:-1])))  # ||C||_1 (C is symmetric)
+    a, b = 1e-3 ** 2, smax ** 2
+    m = CsrLogdet(C.rowptr, C.col, c32, kind="general")
+    m.set_interval(a, b)
+    r = m.estimate(n, M, 0, moments=True)
+    m.close()
+    ref = oracle.estimate(C.rowptr, C.col, c64, a, b, n, M, seed=0, kind=1)
+    dt = np.abs(r["t"] - ref["t"])
+    assert np.all(dt <= moment_tol(d, n)), dt.max()
+    assert abs(r["logdet"] - ref["gamma"] / 2) <= 1e-5 * abs(ref["gamma"] / 2)
+    V = oracle.rademacher(0, d, np.arange(M))
+    g2 = oracle.alg2_literal(C.rowptr, C.col, c64, 1e-3, smax, n, V)
+    assert abs(r["logdet"] - g2) <= 1e-5 * abs(g2)
+    exact = float(np.linalg.slogdet(C.dense())[1])
+    print("paper generator d=%d: gpu %.4f oracle %.4f exact %.4f rel err vs exact %.3e" % (
+        d, r["logdet"], ref["gamma"] / 2, exact, abs(r["logdet"] - exact) / abs(exact)))
+
+
+@pytest.mark.parametrize("kind", ["general", "spd"])
+def test_spanning_trees_apex_graph_matches_oracle(torch, kind):
+    """Spanning-tree counts (Sec. 3.3) with identical probes: the reduced
+    Laplacian L(i*) of a graph with an apex vertex, Algorithm 2 on
+    [1, (2 Delta_max - 1)^2] (kind 'general') or Algorithm 1 on
+    [1, 2 Delta_max - 1] (kind 'spd'); every moment and the estimate of
+    log tau(G) against the oracle."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    L = workloads.apex_graph(2000, 6000, 11)
+    l32, l64 = L.stored("f32")
+    rows = np.repeat(np.arange(L.d), np.diff(L.rowptr))
+    deg_max = float(np.max(l64[L.col == rows]))
+    n, M = (120, 64) if kind == "general" else (60, 64)
+    a, b = (1.0, (2 * deg_max - 1) ** 2) if kind == "general" else (1.0, 2 * deg_max - 1)
+    m = CsrLogdet(L.rowptr, L.col, l32, kind=kind)
+    m.set_interval(a, b)
+    r = m.estimate(n, M, 1, moments=True)
+    m.close()
+    ref = oracle.estimate(L.rowptr, L.col, l64, a, b, n, M, seed=1, kind=1 if kind == "general" else 0)
+    tol = moment_tol(L.d, n)
+    dt = np.abs(r["t"] - ref["t"])
+    assert np.all(dt <= tol), (dt / tol).max()
+    want = ref["gamma"] / 2 if kind == "general" else ref["gamma"]
+    assert abs(r["logdet"] - want) <= 1e-5 * abs(want)
+    print("apex graph %s: max |dt|/tol %.3g" % (kind, (dt / tol).max()))

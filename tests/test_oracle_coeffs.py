@@ -107,4 +107,3 @@ def test_theorem1_worked_example(oracle_mod):
     n_eq1 = next(k for k in range(1, 500) if lhs(k) <= target)
     assert n_formula == n_eq1 == g["formula_n"]
     assert g["paper_printed_n"] == 14 and g["paper_printed_n"] != n_formula
-    assert abs(oracle_mod.thm1_samples(0.1, 0.1) - 54 / 0.01 * np.log(20)) < 1e-9

@@ -320,6 +320,55 @@ def block_diag(mats):
     return blk_rows, Csr(rowptr, col, val, "block_diag(%d)" % len(mats))
 
 
+def paper_sparse_random_device(d: int, seed: int, torch, device="cuda", picks: int = 5):
+    """The recipe of ``paper_sparse_random`` built with torch on the device,
+    for sizes whose numpy construction takes minutes (the benchmark's
+    d = 3e7 timing of Sec. 5.1).  Same distribution, another random stream
+    (torch's Philox on the device), so not the same matrix as the numpy
+    generator at equal seed.  Returns (rowptr int64, col int32, val float64)
+    CUDA tensors with sorted rows and duplicates summed."""
+    g = torch.Generator(device=device).manual_seed(seed)
+    rows = torch.arange(d, device=device, dtype=torch.int64).repeat_interleave(picks)
+    cols = (rows + torch.randint(1, d, rows.shape, device=device, generator=g, dtype=torch.int64)) % d
+    v = torch.rand(rows.shape, device=device, generator=g, dtype=torch.float64) * 2.0 - 1.0
+    diag = torch.arange(d, device=device, dtype=torch.int64)
+    key = torch.cat([rows * d + cols, cols * d + rows, diag * d + diag])
+    val = torch.cat([v, v, torch.zeros(d, device=device, dtype=torch.float64)])
+    del rows, cols, v
+    key, order = torch.sort(key)
+    val = val[order]
+    del order
+    uk, inv = torch.unique_consecutive(key, return_inverse=True)
+    del key
+    sv = torch.zeros(uk.shape, device=device, dtype=torch.float64).index_add_(0, inv, val)
+    del inv, val
+    r = uk // d
+    c = uk % d
+    del uk
+    is_diag = r == c
+    absum = torch.zeros(d, device=device, dtype=torch.float64).index_add_(0, r, torch.where(is_diag, 0.0, sv.abs()))
+    sv = torch.where(is_diag, absum[r] + 1e-3, sv)
+    rowptr = torch.zeros(d + 1, device=device, dtype=torch.int64)
+    rowptr[1:] = torch.cumsum(torch.bincount(r, minlength=d), 0)
+    return rowptr, c.to(torch.int32), sv
+
+
+def grid_pattern_device(N: int, torch, device="cuda"):
+    """The 5-point pattern of ``grid_gmrf`` on an N x N grid in natural
+    row-major order, built on the device: (rowptr int64, col int32,
+    is_diag bool) CUDA tensors."""
+    d = N * N
+    i = torch.arange(d, device=device, dtype=torch.int64)
+    r, c = i // N, i % N
+    cand = torch.stack([i - N, i - 1, i, i + 1, i + N], dim=1)
+    ok = torch.stack([r > 0, c > 0, torch.ones_like(r, dtype=torch.bool), c < N - 1, r < N - 1], dim=1)
+    dg = torch.zeros_like(ok)
+    dg[:, 2] = True
+    rowptr = torch.zeros(d + 1, device=device, dtype=torch.int64)
+    rowptr[1:] = torch.cumsum(ok.sum(dim=1), 0)
+    return rowptr, cand[ok].to(torch.int32), dg[ok]
+
+
 # Named workloads of the benchmark and the parity tests.
 CONFIGS = {
     0: dict(kind="sparse_random_spd", d=2048, picks=3, seed=1000, n=30, M=30, probe_seed=0),
