@@ -777,7 +777,11 @@ def config1_leg(args, torch):
     interval = (cfg["kappa2"], cfg["kappa2"] + 8.0)
     m = CsrLogdet(B.rowptr, B.col, v32)
     m.set_interval(*interval)
-    variant, _ = m.autotune(n, M)
+    if args.variant is None:
+        variant, _ = m.autotune(n, M)
+    else:  # pinned (profiling captures): no autotuner launches
+        variant = args.variant
+        m.set_kernel_variant(variant)
     m.reserve(n, M)
     ms, kernel_ms, launches, _, r = time_estimates(m, n, M, cfg["probe_seed"], interval, max(3, args.steps),
                                                   max(3, args.warmup), torch, 1)
@@ -955,7 +959,7 @@ def main():
                     default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
-    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5],
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5, 6],
                     help="pin the recurrence-step inner-loop variant instead of autotuning it")
     ap.add_argument("--tile-rows", type=int, default=None,
                     help="with --variant and --only batch: rows per work tile of the batched step")

@@ -306,9 +306,21 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *      index, value and address work once per 8 probes (panels of at least 8
  *      probes, else variant 0; batch handles have a wide-lane tile kernel
  *      too).  BF16 values are read as the aligned 4-byte words that hold them
- *      (16-bit loads in the rows that hold the array's first or last entry).
- * The default at creation is 3 when the matrix holds at most 6 stored entries
- * per row on average, else 4 below d = 1e5 and 5 from there (batches: 0).
+ *      (16-bit loads in the rows that hold the array's first or last entry);
+ *   6: staged tiles: a CTA takes tiles of 2048 / P consecutive rows, one
+ *      producer warp copies each tile's row pointers, stored indices and
+ *      values, own rows of w_j, rows of w_{j-1} and sign words into a ring of
+ *      shared-memory stages with bulk asynchronous copies (TMA), and eight
+ *      consumer warps compute with the wide lanes of variant 5, so only the
+ *      gathers stay on a row's chain of dependent loads (for matrices whose
+ *      gathers hit the caches: stencils, point clouds numbered by cell).
+ *      Panels of at least 8 probes and CSR arrays on 16-byte boundaries, else
+ *      variant 5 runs; tiles with more than 16 stored entries per row on
+ *      average read their indices and values from global memory.  Its waits
+ *      are bounded: cld_estimate / cld_grad return CLD_ERR_TIMEOUT if one
+ *      gave up (results invalid).  Single matrices only (batches: 0 to 5).
+ * The default at creation is 6 from d = 1e5 up; below, 3 when the matrix
+ * holds at most 6 stored entries per row on average, else 4 (batches: 0).
  * The variant also sets the grid size, so the last bits of the moments (their
  * summation order) can change with it.
  * Errors: CLD_ERR_INVALID for an unknown variant. */
@@ -325,6 +337,14 @@ CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
  * Returns the chosen variant and its step time in ms (either may be NULL).
  * Errors: CLD_ERR_INVALID, CLD_ERR_NOMEM, CLD_ERR_INTERVAL, CLD_ERR_CUDA. */
 CLD_API cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* ms_out);
+
+/* Testing aid for the bounded waits of variant 6 (no paper counterpart):
+ * with tile > 0, the staged step kernel withholds the copies and arrivals of
+ * row tile tile - 1 (rows (tile-1) T .. tile T - 1, T = 2048 / panel), so the
+ * consumers' waits for that tile run out after about 2 s and cld_estimate
+ * returns CLD_ERR_TIMEOUT; the CUDA context stays usable.  0 (the default)
+ * turns it off.  Errors: CLD_ERR_INVALID for a negative tile. */
+CLD_API cld_status cld_debug_withhold_tile(cld_handle h, int64_t tile);
 
 /* Timing of the dominant kernel (no paper counterpart).  When on, every
  * cld_estimate, and every cld_batch_estimate outside graph mode, records CUDA

@@ -51,6 +51,7 @@ SIGNATURES = [
     ("cld_set_kernel_variant", _i32, [_vp, _i32]),
     ("cld_set_grad_checkpoint", _i32, [_vp, _i32]),
     ("cld_autotune", _i32, [_vp, _i32, _i32, _P(_i32), _P(ctypes.c_float)]),
+    ("cld_debug_withhold_tile", _i32, [_vp, _i64]),
     ("cld_set_profiling", _i32, [_vp, _i32]),
     ("cld_last_timing", _i32, [_vp, _P(ctypes.c_float), _P(_i32), _P(_i32)]),
     ("cld_launch_config", _i32, [_vp, _i32, _P(_i32), _P(_i32), _P(_i32), _P(_i32)]),
@@ -247,6 +248,12 @@ def cld_autotune(h, M, reps=3):
     v, ms = ctypes.c_int(), ctypes.c_float()
     _check(load().cld_autotune(h, M, reps, ctypes.byref(v), ctypes.byref(ms)))
     return v.value, ms.value
+
+
+def cld_debug_withhold_tile(h, tile):
+    """Testing aid of the staged step kernel (variant 6): tile > 0 withholds
+    row tile `tile - 1`, so its bounded waits run out; 0 turns it off."""
+    _check(load().cld_debug_withhold_tile(h, int(tile)))
 
 
 def cld_set_profiling(h, on):

@@ -108,7 +108,7 @@ class CsrLogdet:
     def set_graph(self, on: bool = True):
         B.cld_set_graph(self.h, on)
 
-    def autotune(self, n: int, M: int, reps: int = 3):
+    def autotune(self, n: int, M: int, reps: int = 8):
         """Picks the fastest recurrence-step variant for this matrix (n, M
         size the workspace)."""
         self.reserve(n, M)

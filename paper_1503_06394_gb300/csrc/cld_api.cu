@@ -78,6 +78,7 @@ struct cld_ctx {
 
     int impl = 1;  // recurrence-step inner loop (see step_kernel.cuh)
     int ckpt = 0;  // gradient checkpoint interval K (0: keep every w_j)
+    int64_t withhold_tile = 0;  // testing aid of variant 6 (cld_debug_withhold_tile)
 
     // batch (nb > 0): block-diagonal super matrix, blocks [blk_rows[b], blk_rows[b+1])
     int nb = 0;
@@ -119,11 +120,13 @@ struct Layout {
     int panel, nw, grid, ggrid;
 };
 
-// Inner-loop variant at creation: the shared-memory ring staging the first
-// 5 entries of a row (3) for short rows; otherwise the ring staging 8 (4) for
-// small matrices, where a step is one short burst of rows and latency counts,
-// and the wide lanes (5) from d = 1e5 up, where throughput does.
-static int default_impl(int64_t d, int64_t nnz) { return nnz <= 6 * d ? 3 : d < 100000 ? 4 : 5; }
+// Inner-loop variant at creation: from d = 1e5 up, where throughput counts,
+// the staged tiles (6; measured fastest on GB300 for the random SPD matrix
+// of 11 entries per row, the 5-point grid and the Wendland matrix); below,
+// where a step is one short burst of rows and latency counts, the
+// shared-memory ring staging the first 5 entries of a row (3) for short rows,
+// else the ring staging 8 (4).
+static int default_impl(int64_t d, int64_t nnz) { return d >= 100000 ? 6 : nnz <= 6 * d ? 3 : 4; }
 
 static int panel_for_dense(int M) { return M <= 32 ? 32 : M <= 64 ? 64 : 128; }
 
@@ -135,7 +138,9 @@ static int panel_for(int M) {
 }
 
 static int step_grid(const cld_ctx* h, int panel) {
-    const int rows_per_cta = (kThreads / 32) * (128 / panel);
+    // rows a CTA covers in one pass: 4 probes per lane (the staged tiles of
+    // variant 6: tiles of 2048 / panel rows)
+    const int rows_per_cta = (h->impl == 6 && panel >= 8) ? 2048 / panel : (kThreads / 32) * (128 / panel);
     const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
     const int64_t full = (int64_t)step_ctas_per_sm(panel, (int)h->dtype, h->impl) * h->sms;
     int64_t g = need < full ? need : full;
@@ -272,6 +277,8 @@ static cld_status enqueue_steps(cld_ctx* h, const Layout& L, int n, int M, int p
     a.prm = prm;
     a.mreal = mreal;
     a.impl = h->impl;
+    a.err = at<uint32_t>(h, L.flags) + 1;
+    a.withhold_tile = h->withhold_tile;
     for (int j = j0; j < j1; ++j) {
         // w_{j+1} <- step j; w_j and w_{j-1} from the previous steps (w_0 = v).
         if (events && h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
@@ -814,7 +821,8 @@ cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logde
     }
     cld_status st;
     uint32_t* err = at<uint32_t>(h, L.flags) + 1;
-    if (h->dense) CUDA_TRY(cudaMemsetAsync(err, 0, 4, h->stream));
+    const bool pipelined = h->dense || h->impl == 6;  // kernels with bounded pipeline waits
+    if (pipelined) CUDA_TRY(cudaMemsetAsync(err, 0, 4, h->stream));
     auto body = [&](bool with_seed) {
         return h->dense ? enqueue_dense(h, L, n, M, seed, with_seed) : enqueue_estimate(h, L, n, M, seed, with_seed);
     };
@@ -827,11 +835,13 @@ cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logde
     }
     if (st != CLD_OK) return st;
     uint32_t derr = 0;
-    if (h->dense) CUDA_TRY(cudaMemcpyAsync(&derr, err, 4, cudaMemcpyDeviceToHost, h->stream));
+    if (pipelined) CUDA_TRY(cudaMemcpyAsync(&derr, err, 4, cudaMemcpyDeviceToHost, h->stream));
     Result r{};
     st = read_result(h, L, n, M, logdet_out, stderr_out, moments_out, &r);
     if (st != CLD_OK) return st;
-    if (derr) return fail(CLD_ERR_TIMEOUT, "a dense-step pipeline wait gave up (results invalid)");
+    if (derr)
+        return fail(CLD_ERR_TIMEOUT, "a %s pipeline wait gave up (results invalid)",
+                    h->dense ? "dense-step" : "staged-step");
     if (r.spectrum_bad)
         return fail(CLD_ERR_SPECTRUM,
                     "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]", r.max_ratio,
@@ -876,7 +886,7 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
     int launches = 0, step_launches = 0;
     cld_status st = ensure_events(h, M);
     if (st != CLD_OK) return st;
-    CUDA_TRY(cudaMemsetAsync(flags, 0, 4, h->stream));
+    CUDA_TRY(cudaMemsetAsync(flags, 0, 8, h->stream));  // flags and the pipeline error word
     CUDA_TRY(cudaMemsetAsync(H, 0, (size_t)h->nnz * 4, h->stream));
     CUDA_TRY(launch_set_seed(prm, seed, h->stream));
     CUDA_TRY(launch_coeffs(n, prm, at<double>(h, L.coeffs), at<double>(h, L.coef_scratch), h->stream));
@@ -900,7 +910,7 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         a.prm = prm;
         a.mreal = mreal;
         // the reverse step follows the forward's lane width
-        const bool wide = h->impl == 5 && L.panel >= 8;
+        const bool wide = (h->impl == 5 || h->impl == 6) && L.panel >= 8;
         const int rows_per_cta = (kThreads / 32) * ((wide ? 256 : 128) / L.panel);
         const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
         const int64_t full = (int64_t)adjoint_ctas_per_sm(L.panel, (int)h->dtype, wide) * h->sms;
@@ -958,12 +968,13 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
     }
     h->last_total_launches = launches;
     h->last_step_launches = step_launches;
-    uint32_t f = 0;
-    CUDA_TRY(cudaMemcpyAsync(&f, flags, 4, cudaMemcpyDeviceToHost, h->stream));
+    uint32_t f[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(f, flags, 8, cudaMemcpyDeviceToHost, h->stream));
     Result r{};
     st = read_result(h, L, n, M, logdet_out, nullptr, nullptr, &r);
     if (st != CLD_OK) return st;
-    if (f & 0x10000u) return fail(CLD_ERR_INVALID, "cld_grad needs a structurally symmetric sparsity pattern");
+    if (f[0] & 0x10000u) return fail(CLD_ERR_INVALID, "cld_grad needs a structurally symmetric sparsity pattern");
+    if (f[1]) return fail(CLD_ERR_TIMEOUT, "a staged-step pipeline wait gave up (results invalid)");
     if (r.spectrum_bad)
         return fail(CLD_ERR_SPECTRUM, "max |t_jp|/d = %g exceeds 1: the spectrum is not inside [%g, %g]",
                     r.max_ratio, h->a, h->b);
@@ -1203,6 +1214,8 @@ cld_status cld_set_kernel_variant(cld_handle h, int variant) {
     if (check_handle(h)) return CLD_ERR_INVALID;
     if (variant < 0 || variant >= kNumStepImpls)
         return fail(CLD_ERR_INVALID, "variant must be in [0, %d)", kNumStepImpls);
+    if (h->nb > 0 && variant >= kNumBatchImpls)
+        return fail(CLD_ERR_INVALID, "batch handles take variants 0 .. %d", kNumBatchImpls - 1);
     h->impl = variant;
     return CLD_OK;
 }
@@ -1219,6 +1232,8 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     const int saved_tiles = h->tile_rows;
     int best = -1, best_tiles = saved_tiles;
     float best_ms = 0.f, saved_ms = -1.f;
+    uint32_t* perr = at<uint32_t>(h, make_layout(h, 0, 1, 0).flags) + 1;  // pipeline error word (variant 6)
+    CUDA_TRY(cudaMemsetAsync(perr, 0, 4, h->stream));
     cudaEvent_t e0, e1;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
@@ -1236,7 +1251,7 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
                 return ust;
             }
         }
-        for (int v = 0; v < kNumStepImpls; ++v) {
+        for (int v = 0; v < (h->nb > 0 ? kNumBatchImpls : kNumStepImpls); ++v) {
             h->impl = v;
             const Layout L = make_layout(h, 2, M, 0);
             if (L.total > h->ws_bytes) continue;
@@ -1248,6 +1263,7 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
             a.prm = at<Params>(h, L.params);
             a.mreal = M < L.panel ? M : L.panel;
             a.impl = v;
+            a.err = at<uint32_t>(h, L.flags) + 1;
             const bool general = h->kind == CLD_GENERAL;
             a.rowptr = general ? at<int64_t>(h, L.rowptrT) : h->rowptr;
             a.col = general ? at<int32_t>(h, L.colT) : h->col;
@@ -1296,6 +1312,13 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    uint32_t perr_h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&perr_h, perr, 4, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (perr_h) {
+        h->impl = saved;
+        return fail(CLD_ERR_TIMEOUT, "a staged-step pipeline wait gave up while timing the variants");
+    }
     if (best < 0) {
         h->impl = saved;
         best_tiles = saved_tiles;
@@ -1320,6 +1343,13 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
     return CLD_OK;
 }
 
+cld_status cld_debug_withhold_tile(cld_handle h, int64_t tile) {
+    if (check_handle(h)) return CLD_ERR_INVALID;
+    if (tile < 0) return fail(CLD_ERR_INVALID, "tile must be >= 0");
+    h->withhold_tile = tile;
+    return CLD_OK;
+}
+
 cld_status cld_set_profiling(cld_handle h, int on) {
     if (check_handle(h)) return CLD_ERR_INVALID;
     h->profiling = on != 0;
@@ -1341,9 +1371,11 @@ cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row
     const Layout L = make_layout(h, 1, M, 0);
     if (panel) *panel = L.panel;
     // 4 probes per lane; 8 with the wide lanes (variant 5, panels of 8 or more)
-    if (lanes_per_row) *lanes_per_row = (h->impl == 5 && h->nb == 0 && L.panel >= 8) ? L.panel / 8 : L.panel / 4;
+    const bool wide = (h->impl == 5 || h->impl == 6) && h->nb == 0 && L.panel >= 8;
+    if (lanes_per_row) *lanes_per_row = wide ? L.panel / 8 : L.panel / 4;
     if (ctas) *ctas = L.grid;
-    if (threads) *threads = kThreads;
+    // variant 6: 8 consumer warps and one producer warp
+    if (threads) *threads = (h->impl == 6 && h->nb == 0 && L.panel >= 8) ? 288 : kThreads;
     return CLD_OK;
 }
 

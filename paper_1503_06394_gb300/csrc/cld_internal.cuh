@@ -118,10 +118,11 @@ __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.lau
 // serialization (see pdl_wait): consecutive step launches overlap their
 // launch latency with the predecessor's tail, in streams and in graphs.
 template <typename Arg>
-cudaError_t launch_pdl(void (*kern)(Arg), int grid, int smem, cudaStream_t s, const Arg& arg) {
+cudaError_t launch_pdl(void (*kern)(Arg), int grid, int smem, cudaStream_t s, const Arg& arg,
+                       int threads = kThreads) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -207,9 +208,12 @@ struct StepArgs {
     const Params* prm;
     int mreal;               // real probes in this panel
     int impl;                // inner-loop variant (0..kNumStepImpls-1, see step_kernel.cuh)
+    uint32_t* err;           // variant 6: set (bits) when a pipeline wait gave up
+    int64_t withhold_tile;   // variant 6 testing aid: tile index + 1 never staged (0: none)
 };
 
-constexpr int kNumStepImpls = 6;
+constexpr int kNumStepImpls = 7;
+constexpr int kNumBatchImpls = 6;  // variants with a batched (tile-queue) form
 
 enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
                 kStepFirstFromFloat = 5 };

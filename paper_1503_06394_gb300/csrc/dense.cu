@@ -24,6 +24,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "async_copy.cuh"
 #include "cld_internal.cuh"
 
 namespace cld {
@@ -32,7 +33,6 @@ constexpr int kDRows = 128;     // MMA M: output rows per CTA
 constexpr int kDK = 64;         // K per stage: 64 BF16 = 128 bytes, one swizzle atom
 constexpr int kDSplit = 3;      // parts of the BF16 split of W
 constexpr int kDThreads = 128;  // 4 warps: TMEM lane quarters 0..3
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // a wait gives up after 2 s
 
 struct DenseArgs {
     int64_t d;
@@ -49,44 +49,6 @@ struct DenseArgs {
 };
 
 // ------------------------------------------------------------------ PTX helpers
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Bounded wait on the given phase parity (gives up after kWaitLimitNs of
-// global time); false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    const unsigned long long t0 = global_ns();
-    for (unsigned i = 0;; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n"
-            ".reg .pred p;\n"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            "selp.u32 %0, 1, 0, p;\n"
-            "}\n"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-        if ((i & 255u) == 255u && global_ns() - t0 > kWaitLimitNs) return false;
-    }
-}
-
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"

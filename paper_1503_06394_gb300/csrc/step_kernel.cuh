@@ -446,10 +446,12 @@ constexpr int step_smem() { return ring_bytes(IMPL); }
 
 // Opts kernel K into `bytes` of dynamic shared memory on the current device,
 // once per device (the attribute is per device; ordinals >= 64 set it on
-// every call).  Needed above 48 KB, before the first launch or occupancy query.
+// every call).  Needed when the dynamic and static shared memory together
+// pass 48 KB (`static_bytes`: the kernel's static shared memory, an upper
+// bound is enough), before the first launch or occupancy query.
 template <auto K>
-cudaError_t smem_opt_in(int bytes) {
-    if (bytes <= 48 * 1024) return cudaSuccess;
+cudaError_t smem_opt_in(int bytes, int static_bytes = 0) {
+    if (bytes + static_bytes <= 48 * 1024) return cudaSuccess;
     static std::atomic<unsigned long long> done{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

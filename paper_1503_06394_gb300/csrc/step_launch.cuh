@@ -5,6 +5,7 @@
 #pragma once
 
 #include "step_kernel.cuh"
+#include "step_staged.cuh"
 #include "step_wide.cuh"
 
 namespace cld {
@@ -30,8 +31,49 @@ cudaError_t launch_one_wide(int grid, cudaStream_t s, const StepArgs& a) {
     }
 }
 
+// Variant 6 runs step_kernel_staged (panels of at least 8 probes and CSR
+// arrays on 16-byte boundaries, which its bulk copies need; otherwise the
+// wide lanes of variant 5, whose grid-stride loop covers the same grid).
+// Shape of the staged kernel (variant 6): 4 entries in flight per lane, 8
+// consumer warps, 3 CTAs per SM.  Measured on GB300 against 8 or 6 entries
+// in flight at 2 CTAs per SM and 16 consumer warps at 1 CTA per SM (grid
+// GMRF and Wendland steps): this one is as fast or faster, and four CTAs per
+// SM are slower (the ring's shared memory takes L1 from the gathers).
+template <int I> struct StagedShape;
+template <> struct StagedShape<0> { using C = StagedCfg<4, 8, 3>; };
+
+template <int MP, typename VT, int GATHER, int PREV, int EPI, int I>
+cudaError_t launch_one_staged(int grid, cudaStream_t s, const StepArgs& a) {
+    if constexpr (MP >= 8) {
+        using C = typename StagedShape<I>::C;
+        const bool aligned = (reinterpret_cast<uintptr_t>(a.rowptr) % 16 == 0) &&
+                             (reinterpret_cast<uintptr_t>(a.col) % 16 == 0) &&
+                             (reinterpret_cast<uintptr_t>(a.val) % 16 == 0);
+        if (!aligned || a.err == nullptr) return launch_one_wide<MP, VT, GATHER, PREV, EPI>(grid, s, a);
+        constexpr auto kern = step_kernel_staged<MP, VT, GATHER, PREV, EPI, C>;
+        constexpr int smem = StagedLayout<MP, VT, PREV, EPI, C>::bytes;
+        cudaError_t e = smem_opt_in<kern>(smem, kStagedStaticBytes<MP, C::NC>);
+        if (e != cudaSuccess || grid == 0) return e;
+        return launch_pdl(kern, grid, smem, s, a, C::threads);
+    } else {
+        return launch_one_step<MP, VT, GATHER, PREV, EPI, 0>(grid, s, a);
+    }
+}
+
 template <int MP, typename VT, int IMPL>
 cudaError_t launch_step_impl(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
+    if constexpr (IMPL >= 6) {
+        constexpr int I = IMPL - 6;
+        switch (kind) {
+            case kStepFirst: return launch_one_staged<MP, VT, 1, 0, 1, I>(grid, s, a);
+            case kStepSecond: return launch_one_staged<MP, VT, 0, 1, 1, I>(grid, s, a);
+            case kStepGeneral: return launch_one_staged<MP, VT, 0, 2, 1, I>(grid, s, a);
+            case kProdBits: return launch_one_staged<MP, VT, 1, 0, 0, I>(grid, s, a);
+            case kProdFloat: return launch_one_staged<MP, VT, 0, 0, 0, I>(grid, s, a);
+            case kStepFirstFromFloat: return launch_one_staged<MP, VT, 0, 0, 1, I>(grid, s, a);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if constexpr (IMPL == 5) {
         switch (kind) {
             case kStepFirst: return launch_one_wide<MP, VT, 1, 0, 1>(grid, s, a);
@@ -63,6 +105,7 @@ cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepAr
         case 3: return launch_step_impl<MP, VT, 3>(kind, grid, s, a);
         case 4: return launch_step_impl<MP, VT, 4>(kind, grid, s, a);
         case 5: return launch_step_impl<MP, VT, 5>(kind, grid, s, a);
+        case 6: return launch_step_impl<MP, VT, 6>(kind, grid, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -103,6 +146,21 @@ int ctas_per_sm_wide() {
     }
 }
 
+template <int MP, typename VT, int I>
+int ctas_per_sm_staged() {
+    int n = 0;
+    if constexpr (MP >= 8) {
+        using C = typename StagedShape<I>::C;
+        constexpr auto kern = step_kernel_staged<MP, VT, 0, 2, 1, C>;
+        constexpr int smem = StagedLayout<MP, VT, 2, 1, C>::bytes;
+        if (smem_opt_in<kern>(smem, kStagedStaticBytes<MP, C::NC>) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::threads, smem) != cudaSuccess) return 1;
+        return n > 0 ? n : 1;
+    } else {
+        return ctas_per_sm_impl<MP, VT, 0>();
+    }
+}
+
 template <int MP, typename VT>
 int ctas_per_sm_mp(int impl) {
     switch (impl) {
@@ -112,6 +170,7 @@ int ctas_per_sm_mp(int impl) {
         case 3: return ctas_per_sm_impl<MP, VT, 3>();
         case 4: return ctas_per_sm_impl<MP, VT, 4>();
         case 5: return ctas_per_sm_wide<MP, VT>();
+        case 6: return ctas_per_sm_staged<MP, VT, 0>();
         default: return 1;
     }
 }

@@ -1,0 +1,398 @@
+// Recurrence step with staged tiles (inner-loop variant 6).
+//
+// The same step as step_kernel and step_kernel_wide (Algorithm 1, Sec. 2.2:
+// w_{j+1} = 2 At w_j - w_{j-1} with At applied on the fly, t_{j+1,p} =
+// v_p^T w_{j+1} reduced per CTA), for matrices whose gathers hit the caches
+// (stencils, point clouds numbered by cell, small blocks).  There a row's
+// cost is its chain of dependent loads -- row pointers, then the indices and
+// values of each chunk, then the gathers, then the own row, the w_{j-1} row
+// and the sign word -- not bandwidth.  Here everything but the gathers is
+// streamed into shared memory ahead of use:
+//
+// * a CTA owns tiles of T = 2048 / P consecutive rows (tile blockIdx.x, then
+//   every gridDim.x-th); one producer warp copies a tile's row pointers,
+//   stored indices and values, own rows of w_j, rows of w_{j-1} and sign words
+//   into a ring of NS (2 to 4) shared-memory stages with bulk asynchronous
+//   copies (TMA, cp.async.bulk) that complete on the stage's "full" mbarrier,
+//   up to NS - 1 tiles ahead of the consumers, while
+// * eight consumer warps compute the tiles in order with the wide-lane
+//   mapping of variant 5 (8 consecutive probes per lane, P / 8 lanes per
+//   row, 4 gathers of 32 bytes in flight per lane), write w_{j+1} to global
+//   memory and release the stage on its "empty" mbarrier.  (Two groups of 4
+//   probes per lane, one in each half of the panel, made the shared-memory
+//   reads contiguous but took two 16-byte gathers per entry instead of one
+//   32-byte gather: slower, the L1 data path being the busiest unit.)
+//
+// A tile whose entries do not fit the stage (more than 16 per row on
+// average) is staged without its indices and values, which the consumers
+// then read from global memory.  Bulk copies need 16-byte aligned addresses
+// and sizes: the index and value ranges are widened to 16-byte boundaries
+// (neighbouring rows' entries, never read), and the bytes that would pass
+// the end of the row-pointer, index or value array are copied by plain loads
+// instead.  The launcher uses this variant only when rowptr, col and val are
+// 16-byte aligned.  Every mbarrier wait is bounded and taken by all lanes of
+// a warp, which go on only if all of them saw the phase: a wait that gives up
+// sets args.err and the CTA winds down (the producer first waits, bounded,
+// for the copies still in flight).  Row sums are formed in entry order with
+// the update of recurrence_update, so w_{j+1} is identical to the other
+// variants'.
+#pragma once
+
+#include "async_copy.cuh"
+#include "step_wide.cuh"
+
+namespace cld {
+
+// Shape of one configuration: U stored entries in flight per lane, NC
+// consumer warps per CTA (and one producer warp), MINB resident CTAs per SM.
+template <int U_, int NC_, int MINB_>
+struct StagedCfg {
+    static constexpr int U = U_;
+    static constexpr int NC = NC_;
+    static constexpr int MINB = MINB_;
+    static constexpr int threads = 32 * (NC + 1);
+    // shared memory a CTA may take for its ring (the rest of the SM's 227 KB
+    // stays L1 for the gathers, which need it)
+    static constexpr int budget = MINB >= 3 ? 66 * 1024 : MINB == 2 ? 84 * 1024 : 120 * 1024;
+};
+
+template <int MP, int NC>
+struct StagedGeom {
+    static constexpr int PPL = 8;                      // probes per lane
+    static constexpr int LPR = MP / PPL;               // lanes per row
+    static constexpr int RPW = 32 / LPR;               // rows per consumer warp
+    static constexpr int T = NC * RPW;                 // rows per tile (256 NC / MP)
+    static constexpr int NW = MP <= 32 ? 1 : MP / 32;  // sign words per row
+    static constexpr int CAP = 16 * T;                 // stored entries a stage holds
+};
+
+__host__ __device__ constexpr int staged_up16(int x) { return (x + 15) / 16 * 16; }
+
+// Upper bound of the kernel's static shared memory (moment partials,
+// barriers, stage headers): counted against the 48 KB default limit.
+template <int MP, int NC>
+constexpr int kStagedStaticBytes = NC * MP * 8 + 256;
+
+// Byte offsets of one stage's regions, the stages of the ring and the dynamic
+// shared memory.
+template <int MP, typename VT, int PREV, int EPI, class C>
+struct StagedLayout {
+    using G = StagedGeom<MP, C::NC>;
+    static constexpr bool kOwn = EPI == 1 && PREV != 0;
+    static constexpr bool kPrev = EPI == 1 && PREV == 2;
+    static constexpr bool kSigns = EPI == 1;
+    static constexpr int rp = 0;                                          // T + 2 row pointers
+    static constexpr int col = rp + staged_up16((G::T + 2) * 8);          // CAP indices
+    static constexpr int val = col + staged_up16(G::CAP * 4);             // CAP values
+    static constexpr int own = val + staged_up16(G::CAP * (int)sizeof(VT));
+    static constexpr int prev = own + (kOwn ? G::T * MP * 4 : 0);         // T x P floats each
+    static constexpr int sg = prev + (kPrev ? G::T * MP * 4 : 0);         // T x NW sign words
+    static constexpr int stage = staged_up16(sg + (kSigns ? staged_up16(G::T * G::NW * 4) : 0));
+    // stages in the ring: as many as fit the budget, 2 to 4
+    static constexpr int NS = C::budget / stage >= 4 ? 4 : C::budget / stage >= 3 ? 3 : 2;
+    static constexpr int bytes = NS * stage;
+};
+
+template <typename VT>
+__device__ __forceinline__ uint32_t smem_val_bits(const VT* p);
+template <>
+__device__ __forceinline__ uint32_t smem_val_bits<float>(const float* p) {
+    return __float_as_uint(*p);
+}
+template <>
+__device__ __forceinline__ uint32_t smem_val_bits<double>(const double* p) {
+    return __float_as_uint((float)*p);
+}
+template <>
+__device__ __forceinline__ uint32_t smem_val_bits<bf16_t>(const bf16_t* p) {
+    return (uint32_t)(*reinterpret_cast<const unsigned short*>(p)) << 16;
+}
+
+template <int MP, typename VT, int GATHER, int PREV, int EPI, class C>
+__global__ void __launch_bounds__(C::threads, C::MINB) step_kernel_staged(const StepArgs args) {
+    static_assert(MP >= 8, "staged tiles need at least 8 probes per panel");
+    using G = StagedGeom<MP, C::NC>;
+    using S = StagedLayout<MP, VT, PREV, EPI, C>;
+    constexpr int PPL = G::PPL, LPR = G::LPR, RPW = G::RPW, T = G::T, NW = G::NW, NS = S::NS;
+    constexpr int U = C::U;                   // stored entries in flight per lane
+    constexpr int NC = C::NC;                 // consumer warps
+    constexpr int UV = 16 / (int)sizeof(VT);  // values per 16 bytes
+    // padded probes: signs are masked where v itself enters the result
+    constexpr bool kMask = GATHER == 1 || (EPI == 1 && PREV != 2);
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2 * NS];  // full[0 .. NS), empty[0 .. NS)
+    __shared__ int64_t hdr_kc[NS], hdr_kv[NS];      // first staged index / value entry
+    __shared__ int hdr_staged[NS];
+    __shared__ double red[NC][MP];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[NS + s]); };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full(s), 32);
+            mbar_init(empty(s), NC);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();  // w_j, w_{j-1}, the signs and the parameters come from earlier kernels
+    pdl_trigger();
+
+    const int64_t d = args.d;
+    const int64_t ntiles = (d + T - 1) / T;
+    const int64_t mine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const int64_t* __restrict__ rowptr = args.rowptr;
+
+    if (warp == NC) {
+        // ------------------------------------------------------------ producer
+        const int64_t nnz = __ldg(rowptr + d);
+        int64_t started = 0;         // iterations whose stage was filled (or withheld)
+        int64_t withheld_it = -1;    // the iteration of the withheld tile, if any
+        bool ok = true;
+        int64_t k0 = 0, k1 = 0;
+        if (mine > 0) {
+            const int64_t r0 = (int64_t)blockIdx.x * T;
+            k0 = __ldg(rowptr + r0);
+            k1 = __ldg(rowptr + (r0 + T < d ? r0 + T : d));
+        }
+        for (int64_t i = 0; i < mine; ++i) {
+            const int s = (int)(i % NS);
+            const int64_t use = i / NS;  // how often stage s was filled before
+            // every lane waits; the warp goes on only if all of them saw the phase
+            if (use >= 1 && !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)((use + 1) & 1)))) {
+                ok = false;
+                break;
+            }
+            const int64_t t = (int64_t)blockIdx.x + i * gridDim.x;
+            // testing aid: the withheld tile's stage is never filled, so the
+            // consumers' waits for it run out (see cld_debug_withhold_tile)
+            const bool withhold = args.withhold_tile == t + 1;
+            const int64_t r0 = t * T;
+            const int rows = (int)(d - r0 < T ? d - r0 : T);
+            unsigned char* st = smem + s * S::stage;
+            // row pointers r0 .. r0 + rows
+            uint32_t rp_bulk = (uint32_t)(rows + 1) * 8u;
+            bool rp_tail = false;
+            if (rp_bulk & 15u) {
+                if (r0 + rows + 1 <= d) {
+                    rp_bulk += 8u;  // one more (valid) row pointer
+                } else {
+                    rp_bulk -= 8u;  // the last one by a plain load
+                    rp_tail = true;
+                }
+            }
+            // index and value ranges widened to 16-byte boundaries, clamped at nnz
+            const int64_t ka = k0 & ~(int64_t)3, kz = (k1 + 3) & ~(int64_t)3;
+            const int64_t kzb = kz <= nnz ? kz : (nnz & ~(int64_t)3);
+            const int64_t kva = k0 & ~(int64_t)(UV - 1), kvz = (k1 + UV - 1) & ~(int64_t)(UV - 1);
+            const int64_t kvzb = kvz <= nnz ? kvz : (nnz & ~(int64_t)(UV - 1));
+            const bool staged = kz - ka <= G::CAP && kvz - kva <= G::CAP;
+            const uint32_t col_bytes = staged ? (uint32_t)(kzb - ka) * 4u : 0u;
+            const uint32_t val_bytes = staged ? (uint32_t)(kvzb - kva) * (uint32_t)sizeof(VT) : 0u;
+            const uint32_t vec_bytes = (uint32_t)rows * MP * 4u;
+            const uint32_t sg_bytes = S::kSigns ? (uint32_t)staged_up16(rows * NW * 4) : 0u;
+            if (withhold) {
+                // neither copies nor arrivals for this stage
+            } else if (lane == 0) {
+                hdr_kc[s] = ka;
+                hdr_kv[s] = kva;
+                hdr_staged[s] = staged ? 1 : 0;
+                const uint32_t tx = rp_bulk + col_bytes + val_bytes + (S::kOwn ? vec_bytes : 0u) +
+                                    (S::kPrev ? vec_bytes : 0u) + sg_bytes;
+                mbar_expect_tx(full(s), tx);
+                bulk_g2s(smem_u32(st + S::rp), rowptr + r0, rp_bulk, full(s));
+                if (col_bytes) bulk_g2s(smem_u32(st + S::col), args.col + ka, col_bytes, full(s));
+                if (val_bytes) bulk_g2s(smem_u32(st + S::val), val + kva, val_bytes, full(s));
+                if (S::kOwn) bulk_g2s(smem_u32(st + S::own), args.own + r0 * MP, vec_bytes, full(s));
+                if (S::kPrev) bulk_g2s(smem_u32(st + S::prev), args.wprev + r0 * MP, vec_bytes, full(s));
+                if (S::kSigns) bulk_g2s(smem_u32(st + S::sg), args.vbits + r0 * NW, sg_bytes, full(s));
+            } else {
+                // what the bulk copies leave out at the ends of the arrays
+                if (lane == 1 && rp_tail) reinterpret_cast<int64_t*>(st + S::rp)[rows] = __ldg(rowptr + r0 + rows);
+                if (staged && lane >= 2 && lane < 6) {
+                    const int64_t e = kzb + (lane - 2);
+                    if (e < k1) reinterpret_cast<int32_t*>(st + S::col)[e - ka] = __ldg(args.col + e);
+                }
+                if (staged && lane >= 8 && lane < 8 + UV) {
+                    const int64_t e = kvzb + (lane - 8);
+                    if (e < k1) {
+                        const unsigned short* src = reinterpret_cast<const unsigned short*>(val + e);
+                        unsigned short* dst = reinterpret_cast<unsigned short*>(st + S::val + (e - kva) * sizeof(VT));
+#pragma unroll
+                        for (int h = 0; h < (int)sizeof(VT) / 2; ++h) dst[h] = __ldg(src + h);
+                    }
+                }
+                mbar_arrive(full(s));
+            }
+            if (withhold) withheld_it = i;
+            started = i + 1;
+            // bounds of the next tile, loaded while the stage fills
+            if (i + 1 < mine) {
+                const int64_t rn = (t + gridDim.x) * T;
+                k0 = __ldg(rowptr + rn);
+                k1 = __ldg(rowptr + (rn + T < d ? rn + T : d));
+            }
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(args.err, 1u);
+            // wait (bounded) for the copies of the last NS iterations, which may
+            // still be in flight
+            for (int64_t j = started > NS ? started - NS : 0; j < started; ++j)
+                if (j != withheld_it) mbar_wait(full((int)(j % NS)), (uint32_t)((j / NS) & 1));
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int sub = lane % LPR;
+        const int g_in_w = lane / LPR;
+        const int lr = warp * RPW + g_in_w;  // this lane's row within a tile
+        const int q0 = sub * PPL;
+        const int wsel = q0 >> 5, bsh = q0 & 31;
+        float mk[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) mk[q] = (!kMask || q0 + q < args.mreal) ? 1.f : 0.f;
+        const int64_t kend = value_end<VT>(rowptr, d);
+        float scale = 1.f, scale_lo = 0.f, shift = 0.f, shift_lo = 0.f;
+        if (EPI == 1) {
+            scale = args.prm->scale_hi;
+            scale_lo = args.prm->scale_lo;
+            shift = args.prm->shift_hi;
+            shift_lo = args.prm->shift_lo;
+        }
+        float tacc[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) tacc[q] = 0.f;
+
+        for (int64_t i = 0; i < mine; ++i) {
+            const int s = (int)(i % NS);
+            if (!__all_sync(0xffffffffu, mbar_wait(full(s), (uint32_t)((i / NS) & 1)))) {
+                if (lane == 0) atomicOr(args.err, 2u);
+                break;
+            }
+            const int64_t r0 = ((int64_t)blockIdx.x + i * gridDim.x) * T;
+            const int rows = (int)(d - r0 < T ? d - r0 : T);
+            const unsigned char* st = smem + s * S::stage;
+            if (lr < rows) {
+                const int64_t* rp = reinterpret_cast<const int64_t*>(st + S::rp);
+                const int64_t k0 = rp[lr], k1 = rp[lr + 1];
+                float acc[PPL];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
+                // gathers of U entries whose indices and value bits are in c / ab
+                auto consume = [&](const int (&c)[U], const uint32_t (&ab)[U]) {
+                    float xv[U][PPL];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (c[u] >= 0) {
+                            if (GATHER == 1)
+                                signs8(__ldg(args.vbits + (int64_t)c[u] * NW + wsel), bsh, mk, xv[u]);
+                            else
+                                ldg8(args.x + (int64_t)c[u] * MP + q0, xv[u]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float a = __uint_as_float(ab[u]);
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
+                    }
+                };
+                if (hdr_staged[s]) {
+                    const int32_t* cs = reinterpret_cast<const int32_t*>(st + S::col);
+                    const VT* vs = reinterpret_cast<const VT*>(st + S::val);
+                    const int e0 = (int)(k0 - hdr_kc[s]), e1 = (int)(k1 - hdr_kc[s]);
+                    const int dv = (int)(hdr_kc[s] - hdr_kv[s]);  // value slot = index slot + dv
+                    for (int e = e0; e < e1; e += U) {
+                        int c[U];
+                        uint32_t ab[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const bool ok = e + u < e1;
+                            c[u] = ok ? cs[e + u] : -1;
+                            ab[u] = ok ? smem_val_bits<VT>(vs + e + u + dv) : 0u;
+                        }
+                        consume(c, ab);
+                    }
+                } else {
+                    const bool edge = std::is_same<VT, bf16_t>::value && (k0 == 0 || k1 == kend);
+                    for (int64_t k = k0; k < k1; k += U) {
+                        int c[U];
+                        uint32_t ab[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const bool ok = k + u < k1;
+                            c[u] = ok ? __ldg(args.col + k + u) : -1;
+                            ab[u] = ok ? load_bits(val, k + u, edge) : 0u;
+                        }
+                        consume(c, ab);
+                    }
+                }
+                float res[PPL];
+                if (EPI == 0) {
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) res[q] = acc[q];
+                } else {
+                    float v[PPL], own[PPL], pv[PPL];
+                    const uint32_t* sg = reinterpret_cast<const uint32_t*>(st + S::sg);
+                    signs8(sg[lr * NW + wsel], bsh, mk, v);
+                    if (S::kOwn) {
+                        const float4* o4 = reinterpret_cast<const float4*>(st + S::own + (lr * MP + q0) * 4);
+                        const float4 a = o4[0], b = o4[1];
+                        own[0] = a.x; own[1] = a.y; own[2] = a.z; own[3] = a.w;
+                        own[4] = b.x; own[5] = b.y; own[6] = b.z; own[7] = b.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) own[q] = v[q];
+                    }
+                    if (S::kPrev) {
+                        const float4* p4 = reinterpret_cast<const float4*>(st + S::prev + (lr * MP + q0) * 4);
+                        const float4 a = p4[0], b = p4[1];
+                        pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
+                        pv[4] = b.x; pv[5] = b.y; pv[6] = b.z; pv[7] = b.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) pv[q] = v[q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        res[q] = recurrence_update1<PREV>(acc[q], own[q], pv[q], scale, scale_lo, shift, shift_lo);
+                        tacc[q] = fmaf(v[q], res[q], tacc[q]);
+                    }
+                }
+                const int64_t row = r0 + lr;
+                st4(args.out + row * MP + q0, make_float4(res[0], res[1], res[2], res[3]));
+                st4(args.out + row * MP + q0 + 4, make_float4(res[4], res[5], res[6], res[7]));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty(s));
+        }
+        if (EPI == 1) {
+            // lanes with the same `sub` hold the same probes: fold them
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                double t = tacc[q];
+#pragma unroll
+                for (int off = LPR; off < 32; off <<= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+                if (g_in_w == 0) red[warp][q0 + q] = t;
+            }
+        }
+    }
+    __syncthreads();
+    if (EPI == 1) {
+        // the consumer warps of the CTA in a fixed order
+        for (int p = threadIdx.x; p < MP; p += blockDim.x) {
+            double s = 0.0;
+#pragma unroll
+            for (int w = 0; w < NC; ++w) s += red[w][p];
+            args.tpart[(int64_t)blockIdx.x * MP + p] = s;
+        }
+    }
+}
+
+}  // namespace cld

@@ -21,7 +21,7 @@ def rows_per_lane(m, M):
     return max(1, -(-m.d // groups))
 
 
-def moment_tol(d, n, structured=False, row_terms=16, rows_per_lane=1):
+def moment_tol(d, n, row_terms=16, rows_per_lane=1):
     """|t_gpu - t_oracle| bound for FP32 recurrence vectors against the FP64 oracle.
 
     Each step rounds w_{j+1} entries to FP32 (relative 2^-24 of terms bounded
@@ -42,14 +42,12 @@ def moment_tol(d, n, structured=False, row_terms=16, rows_per_lane=1):
     eps32 L^1.5 / sqrt(3), and the d / L lane sums add these at random, so the
     total is about eps32 L sqrt(d) / sqrt(3).  The bound allows 8 eps32 L sqrt(d).
 
-    ``structured=True`` drops the random-sign assumption: on matrices with a
-    few distinct exactly-representable values (the grid Laplacian) the
-    entries of w_j take few distinct values and their FP32 roundings share a
-    sign, so the errors add up linearly: (j+1)^2 eps32 d."""
+    The same bound holds on the grid Laplacian, whose few distinct, exactly
+    representable values could have made the FP32 roundings share a sign: at
+    d = 1e6 (n = 50, M = 64) the largest moment error measured on GB300 is 0.3
+    of it, on a 64 x 64 grid 0.07."""
     eps = 2.0 ** -24
     j = np.arange(n + 1)[:, None]
     acc = 8.0 * eps * rows_per_lane * np.sqrt(max(d, 1)) if rows_per_lane > 1 else 0.0
-    if structured:
-        return (j + 1) ** 2 * eps * max(d, 1) + 1e-9 * max(d, 1) + acc
     grow = np.sqrt(max(1.0, row_terms / 16.0))
     return 64.0 * (j + 1) ** 2 * eps * np.sqrt(max(d, 1)) * grow + 1e-9 * max(d, 1) + acc

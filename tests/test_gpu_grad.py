@@ -104,11 +104,13 @@ def test_grad_checkpoint_rejects_bad_interval(torch):
     m.close()
 
 
+@pytest.mark.parametrize("variant", [5, 6])
 @pytest.mark.parametrize("kind", ["random", "wendland"])
 @pytest.mark.parametrize("n,M", [(2, 8), (7, 16), (30, 32), (20, 64), (5, 128), (8, 140), (6, 12)])
-def test_grad_wide_lanes_matches_oracle_adjoint(torch, kind, n, M):
-    """With the forward's wide lanes (variant 5) the reverse pass runs its wide
-    form too (8 probes per lane, P >= 8; 1 lane per row at P = 8)."""
+def test_grad_wide_lanes_matches_oracle_adjoint(torch, kind, n, M, variant):
+    """With the forward's wide lanes (variant 5) or staged tiles (variant 6)
+    the reverse pass runs its wide form (8 probes per lane, P >= 8; 1 lane per
+    row at P = 8)."""
     if kind == "random":
         B = workloads.sparse_random_spd(1500, 3, 31)
         v32, v64 = B.stored("f32")
@@ -119,7 +121,7 @@ def test_grad_wide_lanes_matches_oracle_adjoint(torch, kind, n, M):
         B = workloads.Csr(P.rowptr, P.col, val)
         v32, v64 = B.stored("f32")
         a, b = s2, s2 + float(np.max(np.add.reduceat(np.abs(v64), B.rowptr[:-1])))
-    g, G, est = gpu_grad(B, v32, a, b, n, M, seed=n + M, variant=5)
+    g, G, est = gpu_grad(B, v32, a, b, n, M, seed=n + M, variant=variant)
     V = oracle.rademacher(n + M, B.d, np.arange(M))
     Gref = oracle.grad(B.rowptr, B.col, v64, a, b, n, V)
     scale = np.max(np.abs(Gref))
