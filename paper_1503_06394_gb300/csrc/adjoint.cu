@@ -16,6 +16,7 @@
 // mapped through the transpose at the end (no extra gathers).
 #include <math.h>
 
+#include "step_staged.cuh"
 #include "step_wide.cuh"
 
 namespace cld {
@@ -308,6 +309,247 @@ __global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs
     }
 }
 
+// The reverse step with staged tiles (the form of the forward's variant 6):
+// the producer warp of step_kernel_staged copies each tile's row pointers,
+// indices, values and per-entry accumulators H, its rows of w_i,
+// lambda_{i+1} (the row's own entry) and lambda_{i+2}, and its sign words
+// into a ring of shared-memory stages; the consumer warps run the row sweep
+// of adjoint_kernel_wide on them, gathering only lambda_{i+1} rows from
+// global memory, and write H and lambda_i back to global memory.  MODE 1..3
+// (MODE 0 has no gathers and runs the wide form).
+template <int MP, typename VT, int MODE, class C>
+struct AdjStagedLayout {
+    using G = StagedGeom<MP, C::NC>;
+    static constexpr bool kW = MODE != 3;       // w_i rows (MODE 3 uses v)
+    static constexpr bool kOwn = MODE != 3;     // lambda_{i+1} rows
+    static constexpr bool kPrev = MODE == 2;    // lambda_{i+2} rows
+    static constexpr int rp = 0;
+    static constexpr int col = rp + staged_up16((G::T + 2) * 8);
+    static constexpr int h = col + staged_up16(G::CAP * 4);
+    static constexpr int val = h + staged_up16(G::CAP * 4);
+    static constexpr int w = val + staged_up16(G::CAP * (int)sizeof(VT));
+    static constexpr int own = w + (kW ? G::T * MP * 4 : 0);
+    static constexpr int prev = own + (kOwn ? G::T * MP * 4 : 0);
+    static constexpr int sg = prev + (kPrev ? G::T * MP * 4 : 0);
+    static constexpr int stage = staged_up16(sg + staged_up16(G::T * G::NW * 4));
+    static constexpr int NS = C::budget / stage >= 4 ? 4 : C::budget / stage >= 3 ? 3 : 2;
+    static constexpr int bytes = NS * stage;
+};
+
+template <int MP, typename VT, int MODE, class C>
+__global__ void __launch_bounds__(C::threads, C::MINB) adjoint_kernel_staged(const AdjArgs args) {
+    static_assert(MP >= 8 && MODE >= 1 && MODE <= 3, "staged reverse steps: panels of 8 or more, MODE 1..3");
+    using G = StagedGeom<MP, C::NC>;
+    using S = AdjStagedLayout<MP, VT, MODE, C>;
+    constexpr int PPL = G::PPL, LPR = G::LPR, RPW = G::RPW, T = G::T, NW = G::NW, NS = S::NS;
+    constexpr int U = 4;
+    constexpr int NC = C::NC;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2 * NS];
+    __shared__ int64_t hdr_kc[NS], hdr_kv[NS];
+    __shared__ int hdr_staged[NS];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[NS + s]); };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full(s), 32);
+            mbar_init(empty(s), NC);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();  // lambda_{i+1}, lambda_{i+2}, H and w_i come from earlier kernels
+    pdl_trigger();
+
+    const int64_t d = args.d;
+    const int64_t ntiles = (d + T - 1) / T;
+    const int64_t mine = (int64_t)blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const int64_t* __restrict__ rowptr = args.rowptr;
+
+    if (warp == NC) {
+        const int64_t nnz = __ldg(rowptr + d);
+        staged_producer_loop<NS, T>(lane, mine, d, rowptr, args.withhold_tile, args.err, bars,
+                                    [&](int s, uint32_t bar, int64_t r0, int rows, int64_t k0, int64_t k1) {
+            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, bar, r0, rows, d, k0, k1, nnz, G::CAP, rowptr,
+                                         args.col, val, args.H, S::kW ? args.w : nullptr,
+                                         S::kOwn ? args.lam_in : nullptr, S::kPrev ? args.lam_prev : nullptr,
+                                         args.vbits, S::rp, S::col, S::val, S::h, S::w, S::own, S::prev, S::sg,
+                                         hdr_kc[s], hdr_kv[s], hdr_staged[s]);
+        });
+    } else {
+        const int sub = lane % LPR;
+        const int g_in_w = lane / LPR;
+        const unsigned gmask = LPR == 32 ? 0xffffffffu : (((1u << LPR) - 1u) << (g_in_w * LPR));
+        const int lr = warp * RPW + g_in_w;
+        const int q0 = sub * PPL, wsel = q0 >> 5, bsh = q0 & 31;
+        float mk[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) mk[q] = q0 + q < args.mreal ? 1.f : 0.f;
+        const int64_t kend = value_end<VT>(rowptr, d);
+        const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
+        const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
+        const float ci = MODE == 3 ? 0.f : (float)args.coeffs[args.ci];
+        const float hfac = MODE == 3 ? 1.f : 2.f;
+        int qa, qb;  // entries of a chunk whose H update this lane owns
+        adj_owned_entries<LPR>(sub, qa, qb);
+
+        for (int64_t i = 0; i < mine; ++i) {
+            const int s = (int)(i % NS);
+            if (!__all_sync(0xffffffffu, mbar_wait(full(s), (uint32_t)((i / NS) & 1)))) {
+                if (lane == 0) atomicOr(args.err, 2u);
+                break;
+            }
+            const int64_t r0 = ((int64_t)blockIdx.x + i * gridDim.x) * T;
+            const int rows = (int)(d - r0 < T ? d - r0 : T);
+            const unsigned char* st = smem + s * S::stage;
+            if (lr < rows) {
+                const int64_t row = r0 + lr;
+                float v[PPL];
+                signs8(reinterpret_cast<const uint32_t*>(st + S::sg)[lr * NW + wsel], bsh, mk, v);
+                float wk[PPL];
+                if (MODE == 3) {
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) wk[q] = v[q];
+                } else {
+                    const float4* w4 = reinterpret_cast<const float4*>(st + S::w + (lr * MP + q0) * 4);
+                    const float4 a = w4[0], b = w4[1];
+                    wk[0] = a.x; wk[1] = a.y; wk[2] = a.z; wk[3] = a.w;
+                    wk[4] = b.x; wk[5] = b.y; wk[6] = b.z; wk[7] = b.w;
+                }
+                const int64_t* rp = reinterpret_cast<const int64_t*>(st + S::rp);
+                const int64_t k0 = rp[lr], k1 = rp[lr + 1];
+                float acc[PPL];
+#pragma unroll
+                for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
+                // one chunk of U entries starting at global entry k: their
+                // indices c, value bits ab and H values (h1 for LPR == 1, else
+                // this lane's owned entries ha / hb) are given
+                auto chunk = [&](int64_t k, const int (&c)[U], const uint32_t (&ab)[U], const float (&h1)[U],
+                                 float ha, float hb) {
+                    float xv[U][PPL];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        if (c[u] >= 0) {
+                            ldg8(args.lam_in + (int64_t)c[u] * MP + q0, xv[u]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                        }
+                    }
+                    float dt[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const float a = __uint_as_float(ab[u]);
+                        float t = xv[u][0] * wk[0];
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) {
+                            acc[q] = fmaf(a, xv[u][q], acc[q]);
+                            if (q > 0) t = fmaf(xv[u][q], wk[q], t);
+                        }
+                        dt[u] = t;
+                    }
+                    if (LPR == 1) {
+#pragma unroll
+                        for (int u = 0; u < U; ++u)
+                            if (k + u < k1) args.H[k + u] = fmaf(hfac, dt[u], h1[u]);
+                    }
+                    float sa, sb;
+                    adj_reduce_scatter4<LPR>(dt, sub, gmask, sa, sb);
+                    if (qa >= 0 && k + qa < k1) args.H[k + qa] = fmaf(hfac, sa, ha);
+                    if (qb >= 0 && k + qb < k1) args.H[k + qb] = fmaf(hfac, sb, hb);
+                };
+                if (hdr_staged[s]) {
+                    const int32_t* cs = reinterpret_cast<const int32_t*>(st + S::col);
+                    const float* hs = reinterpret_cast<const float*>(st + S::h);
+                    const VT* vs = reinterpret_cast<const VT*>(st + S::val);
+                    const int64_t kc = hdr_kc[s];
+                    const int dv = (int)(kc - hdr_kv[s]);
+                    const int e1 = (int)(k1 - kc);
+                    for (int e = (int)(k0 - kc); e < e1; e += U) {
+                        int c[U];
+                        uint32_t ab[U];
+                        float h1[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const bool ok = e + u < e1;
+                            c[u] = ok ? cs[e + u] : -1;
+                            ab[u] = ok ? smem_val_bits<VT>(vs + e + u + dv) : 0u;
+                            h1[u] = (LPR == 1 && ok) ? hs[e + u] : 0.f;
+                        }
+                        const float ha = (qa >= 0 && e + qa < e1) ? hs[e + qa] : 0.f;
+                        const float hb = (qb >= 0 && e + qb < e1) ? hs[e + qb] : 0.f;
+                        chunk(kc + e, c, ab, h1, ha, hb);
+                    }
+                } else {
+                    const bool edge = std::is_same<VT, bf16_t>::value && (k0 == 0 || k1 == kend);
+                    for (int64_t k = k0; k < k1; k += U) {
+                        int c[U];
+                        uint32_t ab[U];
+                        float h1[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const bool ok = k + u < k1;
+                            c[u] = ok ? __ldg(args.col + k + u) : -1;
+                            ab[u] = ok ? load_bits(val, k + u, edge) : 0u;
+                            h1[u] = (LPR == 1 && ok) ? args.H[k + u] : 0.f;
+                        }
+                        const float ha = (qa >= 0 && k + qa < k1) ? args.H[k + qa] : 0.f;
+                        const float hb = (qb >= 0 && k + qb < k1) ? args.H[k + qb] : 0.f;
+                        chunk(k, c, ab, h1, ha, hb);
+                    }
+                }
+                if (MODE != 3) {
+                    float own[PPL], pv[PPL];
+                    const float4* o4 = reinterpret_cast<const float4*>(st + S::own + (lr * MP + q0) * 4);
+                    {
+                        const float4 a = o4[0], b = o4[1];
+                        own[0] = a.x; own[1] = a.y; own[2] = a.z; own[3] = a.w;
+                        own[4] = b.x; own[5] = b.y; own[6] = b.z; own[7] = b.w;
+                    }
+                    if (MODE == 2) {
+                        const float4* p4 = reinterpret_cast<const float4*>(st + S::prev + (lr * MP + q0) * 4);
+                        const float4 a = p4[0], b = p4[1];
+                        pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
+                        pv[4] = b.x; pv[5] = b.y; pv[6] = b.z; pv[7] = b.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) pv[q] = 0.f;
+                    }
+                    float out[PPL];
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        const float y = fmaf(scale, acc[q], -shift * own[q]) + fmaf(scale_lo, acc[q], -shift_lo * own[q]);
+                        out[q] = fmaf(ci, v[q], fmaf(2.f, y, -pv[q]));
+                    }
+                    st4(args.lam_out + row * MP + q0, make_float4(out[0], out[1], out[2], out[3]));
+                    st4(args.lam_out + row * MP + q0 + 4, make_float4(out[4], out[5], out[6], out[7]));
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(empty(s));
+        }
+    }
+    __syncthreads();
+}
+
+// Shape of the staged reverse step: as the forward's variant 6.
+using AdjStagedCfg = StagedCfg<4, 8, 3>;
+
+template <int MP, typename VT, int MODE>
+static cudaError_t launch_adj_staged_one(int grid, cudaStream_t s, const AdjArgs& a) {
+    using C = AdjStagedCfg;
+    constexpr auto kern = adjoint_kernel_staged<MP, VT, MODE, C>;
+    constexpr int smem = AdjStagedLayout<MP, VT, MODE, C>::bytes;
+    cudaError_t e = smem_opt_in<kern>(smem, 256);
+    if (e != cudaSuccess || grid == 0) return e;
+    return launch_pdl(kern, grid, smem, s, a, C::threads);
+}
+
 template <int MP, typename VT>
 static cudaError_t launch_adj_wide_mp(int mode, int grid, cudaStream_t s, const AdjArgs& a) {
     if constexpr (MP >= 8) {
@@ -334,9 +576,39 @@ static cudaError_t launch_adj_mp(int mode, int grid, cudaStream_t s, const AdjAr
     }
 }
 
+template <int MP, typename VT>
+static cudaError_t launch_adj_staged_mp(int mode, int grid, cudaStream_t s, const AdjArgs& a) {
+    if constexpr (MP >= 8) {
+        // bulk copies need 16-byte aligned CSR arrays; MODE 0 has no gathers
+        const bool aligned = (reinterpret_cast<uintptr_t>(a.rowptr) % 16 == 0) &&
+                             (reinterpret_cast<uintptr_t>(a.col) % 16 == 0) &&
+                             (reinterpret_cast<uintptr_t>(a.val) % 16 == 0) &&
+                             (reinterpret_cast<uintptr_t>(a.H) % 16 == 0);
+        if (mode == 0 || !aligned || a.err == nullptr) return launch_adj_wide_mp<MP, VT>(mode, grid, s, a);
+        switch (mode) {
+            case 1: return launch_adj_staged_one<MP, VT, 1>(grid, s, a);
+            case 2: return launch_adj_staged_one<MP, VT, 2>(grid, s, a);
+            case 3: return launch_adj_staged_one<MP, VT, 3>(grid, s, a);
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        return cudaErrorInvalidValue;
+    }
+}
+
 template <typename VT>
-static cudaError_t launch_adj_vt(int panel, int mode, int grid, cudaStream_t s, const AdjArgs& a, bool wide) {
-    if (wide) {
+static cudaError_t launch_adj_vt(int panel, int mode, int grid, cudaStream_t s, const AdjArgs& a, int form) {
+    if (form == 2) {
+        switch (panel) {
+            case 8: return launch_adj_staged_mp<8, VT>(mode, grid, s, a);
+            case 16: return launch_adj_staged_mp<16, VT>(mode, grid, s, a);
+            case 32: return launch_adj_staged_mp<32, VT>(mode, grid, s, a);
+            case 64: return launch_adj_staged_mp<64, VT>(mode, grid, s, a);
+            case 128: return launch_adj_staged_mp<128, VT>(mode, grid, s, a);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (form == 1) {
         switch (panel) {
             case 8: return launch_adj_wide_mp<8, VT>(mode, grid, s, a);
             case 16: return launch_adj_wide_mp<16, VT>(mode, grid, s, a);
@@ -380,12 +652,21 @@ __global__ void adjoint_gather_kernel(int64_t d, const int64_t* __restrict__ row
 }
 
 template <int MP, typename VT>
-static int adj_ctas_mp(bool wide) {
+static int adj_ctas_mp(int form) {
     int n = 0;
     cudaError_t e;
     if constexpr (MP >= 8) {
-        e = wide ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel_wide<MP, VT, 2>, kThreads, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0);
+        if (form == 2) {
+            using C = AdjStagedCfg;
+            constexpr auto kern = adjoint_kernel_staged<MP, VT, 2, C>;
+            constexpr int smem = AdjStagedLayout<MP, VT, 2, C>::bytes;
+            e = smem_opt_in<kern>(smem, 256);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::threads, smem);
+        } else {
+            e = form == 1
+                    ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel_wide<MP, VT, 2>, kThreads, 0)
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0);
+        }
     } else {
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, adjoint_kernel<MP, VT, 2>, kThreads, 0);
     }
@@ -394,32 +675,32 @@ static int adj_ctas_mp(bool wide) {
 }
 
 template <typename VT>
-static int adj_ctas_vt(int panel, bool wide) {
+static int adj_ctas_vt(int panel, int form) {
     switch (panel) {
-        case 4: return adj_ctas_mp<4, VT>(false);
-        case 8: return adj_ctas_mp<8, VT>(wide);
-        case 16: return adj_ctas_mp<16, VT>(wide);
-        case 32: return adj_ctas_mp<32, VT>(wide);
-        case 64: return adj_ctas_mp<64, VT>(wide);
-        case 128: return adj_ctas_mp<128, VT>(wide);
+        case 4: return adj_ctas_mp<4, VT>(0);
+        case 8: return adj_ctas_mp<8, VT>(form);
+        case 16: return adj_ctas_mp<16, VT>(form);
+        case 32: return adj_ctas_mp<32, VT>(form);
+        case 64: return adj_ctas_mp<64, VT>(form);
+        case 128: return adj_ctas_mp<128, VT>(form);
         default: return 1;
     }
 }
 
-int adjoint_ctas_per_sm(int panel, int dtype, bool wide) {
+int adjoint_ctas_per_sm(int panel, int dtype, int form) {
     switch (dtype) {
-        case 0: return adj_ctas_vt<float>(panel, wide);
-        case 1: return adj_ctas_vt<bf16_t>(panel, wide);
-        case 2: return adj_ctas_vt<double>(panel, wide);
+        case 0: return adj_ctas_vt<float>(panel, form);
+        case 1: return adj_ctas_vt<bf16_t>(panel, form);
+        case 2: return adj_ctas_vt<double>(panel, form);
         default: return 1;
     }
 }
 
-cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, bool wide) {
+cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, int form) {
     switch (dtype) {
-        case 0: return launch_adj_vt<float>(panel, mode, grid, s, a, wide);
-        case 1: return launch_adj_vt<bf16_t>(panel, mode, grid, s, a, wide);
-        case 2: return launch_adj_vt<double>(panel, mode, grid, s, a, wide);
+        case 0: return launch_adj_vt<float>(panel, mode, grid, s, a, form);
+        case 1: return launch_adj_vt<bf16_t>(panel, mode, grid, s, a, form);
+        case 2: return launch_adj_vt<double>(panel, mode, grid, s, a, form);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -909,11 +909,15 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         a.coeffs = at<double>(h, L.coeffs);
         a.prm = prm;
         a.mreal = mreal;
-        // the reverse step follows the forward's lane width
-        const bool wide = (h->impl == 5 || h->impl == 6) && L.panel >= 8;
-        const int rows_per_cta = (kThreads / 32) * ((wide ? 256 : 128) / L.panel);
+        a.err = flags + 1;
+        a.withhold_tile = h->withhold_tile;
+        // the reverse step follows the forward's form: per-lane, wide lanes
+        // (variant 5) or staged tiles (variant 6; both cover 2048 / panel rows
+        // per CTA pass)
+        const int form = L.panel < 8 ? 0 : h->impl == 6 ? 2 : h->impl == 5 ? 1 : 0;
+        const int rows_per_cta = (kThreads / 32) * ((form > 0 ? 256 : 128) / L.panel);
         const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
-        const int64_t full = (int64_t)adjoint_ctas_per_sm(L.panel, (int)h->dtype, wide) * h->sms;
+        const int64_t full = (int64_t)adjoint_ctas_per_sm(L.panel, (int)h->dtype, form) * h->sms;
         const int agrid = (int)(need < full ? (need > 0 ? need : 1) : full);
         // lambda_i lives in lam[i % 3]; reverse steps i = n, n-1, ..., 1, step
         // i < n reading w_i
@@ -924,7 +928,7 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
             a.lam_prev = lam[(i + 2) % 3];
             a.w = i <= n - 1 ? wbuf(h, L, i, wm) : nullptr;
             const int mode = i == n ? 0 : i == n - 1 ? 1 : 2;
-            CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, mode, agrid, h->stream, a, wide));
+            CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, mode, agrid, h->stream, a, form));
             ++launches;
             return CLD_OK;
         };
@@ -954,7 +958,7 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         a.lam_in = lam[1 % 3];  // lambda_1
         a.lam_out = nullptr;
         a.w = nullptr;
-        CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, 3, agrid, h->stream, a, wide));
+        CUDA_TRY(launch_adjoint(L.panel, (int)h->dtype, 3, agrid, h->stream, a, form));
         ++launches;
     }
     CUDA_TRY(launch_finalize(n, M, h->d, 0, prm, at<double>(h, L.T), at<double>(h, L.coeffs),

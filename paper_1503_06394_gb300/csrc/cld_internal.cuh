@@ -321,11 +321,14 @@ struct AdjArgs {
     int ci;                  // i
     const Params* prm;
     int mreal;
+    uint32_t* err;           // staged form: set when a pipeline wait gave up
+    int64_t withhold_tile;   // staged form testing aid (as StepArgs::withhold_tile)
 };
-// wide: the wide-lane reverse step (8 probes per lane, panels of at least 8),
-// used when the forward runs variant 5.
-cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, bool wide);
-int adjoint_ctas_per_sm(int panel, int dtype, bool wide);
+// form: 0 the per-lane reverse step; 1 the wide-lane one (8 probes per lane,
+// panels of at least 8), used when the forward runs variant 5; 2 the staged
+// tiles (variant 6's form; the wide one where it cannot run).
+cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, int form);
+int adjoint_ctas_per_sm(int panel, int dtype, int form);
 cudaError_t launch_adjoint_gather(int64_t d, const int64_t* rowptr, const int32_t* col, const float* H,
                                   double gscale, float* G, uint32_t* flags, int grid, cudaStream_t s);
 

@@ -108,6 +108,137 @@ __device__ __forceinline__ uint32_t smem_val_bits<bf16_t>(const bf16_t* p) {
     return (uint32_t)(*reinterpret_cast<const unsigned short*>(p)) << 16;
 }
 
+// Bounds and copies of one tile for the producer warp: row pointers
+// r0 .. r0 + rows, the stored indices and values of entries [k0, k1) (and, with
+// H, the per-entry FP32 accumulators of the same range), up to three blocks of
+// `rows` x MP floats starting at row r0, and the rows' sign words, into the
+// stage at `st` (byte offsets o_*; a null source or a negative offset: not
+// staged).  Lane 0 registers the bytes on the stage's mbarrier and issues the
+// bulk copies; lanes 1 .. 15 copy what the bulk copies must leave out at the
+// ends of the arrays; every lane then arrives once (the barrier expects 32).
+// The index range is widened to 16-byte boundaries; if it holds more than
+// cap entries, indices, values and H stay in global memory (hdr_staged = 0).
+template <int MP, int NW, typename VT>
+__device__ __forceinline__ void staged_fill_tile(int lane, unsigned char* st, uint32_t bar, int64_t r0, int rows,
+                                                 int64_t d, int64_t k0, int64_t k1, int64_t nnz, int cap,
+                                                 const int64_t* rowptr, const int32_t* col, const VT* val,
+                                                 const float* H, const float* v0, const float* v1, const float* v2,
+                                                 const uint32_t* vbits, int o_rp, int o_col, int o_val, int o_h,
+                                                 int o_v0, int o_v1, int o_v2, int o_sg, int64_t& hdr_kc,
+                                                 int64_t& hdr_kv, int& hdr_staged) {
+    constexpr int UV = 16 / (int)sizeof(VT);  // values per 16 bytes
+    // row pointers r0 .. r0 + rows
+    uint32_t rp_bulk = (uint32_t)(rows + 1) * 8u;
+    bool rp_tail = false;
+    if (rp_bulk & 15u) {
+        if (r0 + rows + 1 <= d) {
+            rp_bulk += 8u;  // one more (valid) row pointer
+        } else {
+            rp_bulk -= 8u;  // the last one by a plain load
+            rp_tail = true;
+        }
+    }
+    // index and value ranges widened to 16-byte boundaries, clamped at nnz
+    const int64_t ka = k0 & ~(int64_t)3, kz = (k1 + 3) & ~(int64_t)3;
+    const int64_t kzb = kz <= nnz ? kz : (nnz & ~(int64_t)3);
+    const int64_t kva = k0 & ~(int64_t)(UV - 1), kvz = (k1 + UV - 1) & ~(int64_t)(UV - 1);
+    const int64_t kvzb = kvz <= nnz ? kvz : (nnz & ~(int64_t)(UV - 1));
+    const bool staged = kz - ka <= cap && kvz - kva <= cap;
+    const uint32_t col_bytes = staged ? (uint32_t)(kzb - ka) * 4u : 0u;
+    const uint32_t h_bytes = H != nullptr ? col_bytes : 0u;
+    const uint32_t val_bytes = staged ? (uint32_t)(kvzb - kva) * (uint32_t)sizeof(VT) : 0u;
+    const uint32_t vec_bytes = (uint32_t)rows * MP * 4u;
+    const uint32_t sg_bytes = o_sg >= 0 ? (uint32_t)staged_up16(rows * NW * 4) : 0u;
+    if (lane == 0) {
+        hdr_kc = ka;
+        hdr_kv = kva;
+        hdr_staged = staged ? 1 : 0;
+        const uint32_t tx = rp_bulk + col_bytes + h_bytes + val_bytes + (v0 ? vec_bytes : 0u) +
+                            (v1 ? vec_bytes : 0u) + (v2 ? vec_bytes : 0u) + sg_bytes;
+        mbar_expect_tx(bar, tx);
+        bulk_g2s(smem_u32(st + o_rp), rowptr + r0, rp_bulk, bar);
+        if (col_bytes) bulk_g2s(smem_u32(st + o_col), col + ka, col_bytes, bar);
+        if (h_bytes) bulk_g2s(smem_u32(st + o_h), H + ka, h_bytes, bar);
+        if (val_bytes) bulk_g2s(smem_u32(st + o_val), val + kva, val_bytes, bar);
+        if (v0) bulk_g2s(smem_u32(st + o_v0), v0 + r0 * MP, vec_bytes, bar);
+        if (v1) bulk_g2s(smem_u32(st + o_v1), v1 + r0 * MP, vec_bytes, bar);
+        if (v2) bulk_g2s(smem_u32(st + o_v2), v2 + r0 * MP, vec_bytes, bar);
+        if (sg_bytes) bulk_g2s(smem_u32(st + o_sg), vbits + r0 * NW, sg_bytes, bar);
+    } else {
+        if (lane == 1 && rp_tail) reinterpret_cast<int64_t*>(st + o_rp)[rows] = __ldg(rowptr + r0 + rows);
+        if (staged && lane >= 2 && lane < 6) {
+            const int64_t e = kzb + (lane - 2);
+            if (e < k1) {
+                reinterpret_cast<int32_t*>(st + o_col)[e - ka] = __ldg(col + e);
+                if (H != nullptr) reinterpret_cast<float*>(st + o_h)[e - ka] = H[e];
+            }
+        }
+        if (staged && lane >= 8 && lane < 8 + UV) {
+            const int64_t e = kvzb + (lane - 8);
+            if (e < k1) {
+                const unsigned short* src = reinterpret_cast<const unsigned short*>(val + e);
+                unsigned short* dst = reinterpret_cast<unsigned short*>(st + o_val + (e - kva) * sizeof(VT));
+#pragma unroll
+                for (int h = 0; h < (int)sizeof(VT) / 2; ++h) dst[h] = __ldg(src + h);
+            }
+        }
+        mbar_arrive(bar);
+    }
+}
+
+// The producer warp's loop over the CTA's tiles (blockIdx.x, then every
+// gridDim.x-th): wait until the stage is free (bounded, all lanes), fill it
+// with fill(stage, tile, r0, rows, k0, k1), and load the next tile's entry
+// bounds while the copies fly.  A tile equal to withhold_tile - 1 is neither
+// copied nor announced (a testing aid: its consumers' waits run out).  If a
+// wait gives up: set bit 0 of *err and wait (bounded) for the copies of the
+// last NS iterations, which may still be in flight.
+template <int NS, int T, class Fill>
+__device__ __forceinline__ void staged_producer_loop(int lane, int64_t mine, int64_t d, const int64_t* rowptr,
+                                                     int64_t withhold_tile, uint32_t* err, const uint64_t* bars,
+                                                     Fill&& fill) {
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[NS + s]); };
+    int64_t started = 0;       // iterations whose stage was filled (or withheld)
+    int64_t withheld_it = -1;  // the iteration of the withheld tile, if any
+    bool ok = true;
+    int64_t k0 = 0, k1 = 0;
+    if (mine > 0) {
+        const int64_t r0 = (int64_t)blockIdx.x * T;
+        k0 = __ldg(rowptr + r0);
+        k1 = __ldg(rowptr + (r0 + T < d ? r0 + T : d));
+    }
+    for (int64_t i = 0; i < mine; ++i) {
+        const int s = (int)(i % NS);
+        const int64_t use = i / NS;  // how often stage s was filled before
+        // every lane waits; the warp goes on only if all of them saw the phase
+        if (use >= 1 && !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)((use + 1) & 1)))) {
+            ok = false;
+            break;
+        }
+        const int64_t t = (int64_t)blockIdx.x + i * gridDim.x;
+        const int64_t r0 = t * T;
+        const int rows = (int)(d - r0 < T ? d - r0 : T);
+        if (withhold_tile == t + 1) {
+            withheld_it = i;  // neither copies nor arrivals for this stage
+        } else {
+            fill(s, full(s), r0, rows, k0, k1);
+        }
+        started = i + 1;
+        // bounds of the next tile, loaded while the stage fills
+        if (i + 1 < mine) {
+            const int64_t rn = (t + gridDim.x) * T;
+            k0 = __ldg(rowptr + rn);
+            k1 = __ldg(rowptr + (rn + T < d ? rn + T : d));
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(err, 1u);
+        for (int64_t j = started > NS ? started - NS : 0; j < started; ++j)
+            if (j != withheld_it) mbar_wait(full((int)(j % NS)), (uint32_t)((j / NS) & 1));
+    }
+}
+
 template <int MP, typename VT, int GATHER, int PREV, int EPI, class C>
 __global__ void __launch_bounds__(C::threads, C::MINB) step_kernel_staged(const StepArgs args) {
     static_assert(MP >= 8, "staged tiles need at least 8 probes per panel");
@@ -116,7 +247,6 @@ __global__ void __launch_bounds__(C::threads, C::MINB) step_kernel_staged(const 
     constexpr int PPL = G::PPL, LPR = G::LPR, RPW = G::RPW, T = G::T, NW = G::NW, NS = S::NS;
     constexpr int U = C::U;                   // stored entries in flight per lane
     constexpr int NC = C::NC;                 // consumer warps
-    constexpr int UV = 16 / (int)sizeof(VT);  // values per 16 bytes
     // padded probes: signs are masked where v itself enters the result
     constexpr bool kMask = GATHER == 1 || (EPI == 1 && PREV != 2);
 
@@ -150,100 +280,14 @@ __global__ void __launch_bounds__(C::threads, C::MINB) step_kernel_staged(const 
     if (warp == NC) {
         // ------------------------------------------------------------ producer
         const int64_t nnz = __ldg(rowptr + d);
-        int64_t started = 0;         // iterations whose stage was filled (or withheld)
-        int64_t withheld_it = -1;    // the iteration of the withheld tile, if any
-        bool ok = true;
-        int64_t k0 = 0, k1 = 0;
-        if (mine > 0) {
-            const int64_t r0 = (int64_t)blockIdx.x * T;
-            k0 = __ldg(rowptr + r0);
-            k1 = __ldg(rowptr + (r0 + T < d ? r0 + T : d));
-        }
-        for (int64_t i = 0; i < mine; ++i) {
-            const int s = (int)(i % NS);
-            const int64_t use = i / NS;  // how often stage s was filled before
-            // every lane waits; the warp goes on only if all of them saw the phase
-            if (use >= 1 && !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)((use + 1) & 1)))) {
-                ok = false;
-                break;
-            }
-            const int64_t t = (int64_t)blockIdx.x + i * gridDim.x;
-            // testing aid: the withheld tile's stage is never filled, so the
-            // consumers' waits for it run out (see cld_debug_withhold_tile)
-            const bool withhold = args.withhold_tile == t + 1;
-            const int64_t r0 = t * T;
-            const int rows = (int)(d - r0 < T ? d - r0 : T);
-            unsigned char* st = smem + s * S::stage;
-            // row pointers r0 .. r0 + rows
-            uint32_t rp_bulk = (uint32_t)(rows + 1) * 8u;
-            bool rp_tail = false;
-            if (rp_bulk & 15u) {
-                if (r0 + rows + 1 <= d) {
-                    rp_bulk += 8u;  // one more (valid) row pointer
-                } else {
-                    rp_bulk -= 8u;  // the last one by a plain load
-                    rp_tail = true;
-                }
-            }
-            // index and value ranges widened to 16-byte boundaries, clamped at nnz
-            const int64_t ka = k0 & ~(int64_t)3, kz = (k1 + 3) & ~(int64_t)3;
-            const int64_t kzb = kz <= nnz ? kz : (nnz & ~(int64_t)3);
-            const int64_t kva = k0 & ~(int64_t)(UV - 1), kvz = (k1 + UV - 1) & ~(int64_t)(UV - 1);
-            const int64_t kvzb = kvz <= nnz ? kvz : (nnz & ~(int64_t)(UV - 1));
-            const bool staged = kz - ka <= G::CAP && kvz - kva <= G::CAP;
-            const uint32_t col_bytes = staged ? (uint32_t)(kzb - ka) * 4u : 0u;
-            const uint32_t val_bytes = staged ? (uint32_t)(kvzb - kva) * (uint32_t)sizeof(VT) : 0u;
-            const uint32_t vec_bytes = (uint32_t)rows * MP * 4u;
-            const uint32_t sg_bytes = S::kSigns ? (uint32_t)staged_up16(rows * NW * 4) : 0u;
-            if (withhold) {
-                // neither copies nor arrivals for this stage
-            } else if (lane == 0) {
-                hdr_kc[s] = ka;
-                hdr_kv[s] = kva;
-                hdr_staged[s] = staged ? 1 : 0;
-                const uint32_t tx = rp_bulk + col_bytes + val_bytes + (S::kOwn ? vec_bytes : 0u) +
-                                    (S::kPrev ? vec_bytes : 0u) + sg_bytes;
-                mbar_expect_tx(full(s), tx);
-                bulk_g2s(smem_u32(st + S::rp), rowptr + r0, rp_bulk, full(s));
-                if (col_bytes) bulk_g2s(smem_u32(st + S::col), args.col + ka, col_bytes, full(s));
-                if (val_bytes) bulk_g2s(smem_u32(st + S::val), val + kva, val_bytes, full(s));
-                if (S::kOwn) bulk_g2s(smem_u32(st + S::own), args.own + r0 * MP, vec_bytes, full(s));
-                if (S::kPrev) bulk_g2s(smem_u32(st + S::prev), args.wprev + r0 * MP, vec_bytes, full(s));
-                if (S::kSigns) bulk_g2s(smem_u32(st + S::sg), args.vbits + r0 * NW, sg_bytes, full(s));
-            } else {
-                // what the bulk copies leave out at the ends of the arrays
-                if (lane == 1 && rp_tail) reinterpret_cast<int64_t*>(st + S::rp)[rows] = __ldg(rowptr + r0 + rows);
-                if (staged && lane >= 2 && lane < 6) {
-                    const int64_t e = kzb + (lane - 2);
-                    if (e < k1) reinterpret_cast<int32_t*>(st + S::col)[e - ka] = __ldg(args.col + e);
-                }
-                if (staged && lane >= 8 && lane < 8 + UV) {
-                    const int64_t e = kvzb + (lane - 8);
-                    if (e < k1) {
-                        const unsigned short* src = reinterpret_cast<const unsigned short*>(val + e);
-                        unsigned short* dst = reinterpret_cast<unsigned short*>(st + S::val + (e - kva) * sizeof(VT));
-#pragma unroll
-                        for (int h = 0; h < (int)sizeof(VT) / 2; ++h) dst[h] = __ldg(src + h);
-                    }
-                }
-                mbar_arrive(full(s));
-            }
-            if (withhold) withheld_it = i;
-            started = i + 1;
-            // bounds of the next tile, loaded while the stage fills
-            if (i + 1 < mine) {
-                const int64_t rn = (t + gridDim.x) * T;
-                k0 = __ldg(rowptr + rn);
-                k1 = __ldg(rowptr + (rn + T < d ? rn + T : d));
-            }
-        }
-        if (!ok) {
-            if (lane == 0) atomicOr(args.err, 1u);
-            // wait (bounded) for the copies of the last NS iterations, which may
-            // still be in flight
-            for (int64_t j = started > NS ? started - NS : 0; j < started; ++j)
-                if (j != withheld_it) mbar_wait(full((int)(j % NS)), (uint32_t)((j / NS) & 1));
-        }
+        staged_producer_loop<NS, T>(lane, mine, d, rowptr, args.withhold_tile, args.err, bars,
+                                    [&](int s, uint32_t bar, int64_t r0, int rows, int64_t k0, int64_t k1) {
+            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, bar, r0, rows, d, k0, k1, nnz, G::CAP, rowptr,
+                                         args.col, val, nullptr, S::kOwn ? args.own : nullptr,
+                                         S::kPrev ? args.wprev : nullptr, nullptr, args.vbits, S::rp, S::col,
+                                         S::val, -1, S::own, S::prev, -1, S::kSigns ? S::sg : -1, hdr_kc[s],
+                                         hdr_kv[s], hdr_staged[s]);
+        });
     } else {
         // ------------------------------------------------------------ consumers
         const int sub = lane % LPR;
