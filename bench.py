@@ -256,7 +256,7 @@ def run_only(args):
            "gmrf": gmrf_leg, "config1": config1_leg, "batch": batch_leg}[args.only]
     out = leg(args, torch, 1) if args.only == "adjoint" else leg(args, torch)
     key = {"config1": "gmrf_config1"}.get(args.only, args.only)
-    if not args.no_cpu_baseline and key in ("latency", "gmrf_config1", "paper", "gmrf"):
+    if not args.no_cpu_baseline and key in ("latency", "gmrf_config1", "paper", "gmrf", "dense"):
         reference_errors({key: out})
     print(json.dumps({"only": args.only, **out}), flush=True)
 
@@ -866,6 +866,11 @@ def reference_errors(line):
                                        for e in gm["sweep"] if e["logdet_exact"] != 0)
         gm["max_err_in_stderrs"] = max(abs(e["logdet"] - e["logdet_exact"]) / e["stderr"] for e in gm["sweep"]
                                        if e["stderr"] > 0)
+    dn = line.get("dense")
+    if dn is not None:
+        exact = oracle.kms_logdet(dn["d"], dn["rho"])
+        dn.update({"exact_closed_form": exact, "rel_err_vs_exact": abs(dn["logdet"] - exact) / abs(exact),
+                   "err_in_stderrs": abs(dn["logdet"] - exact) / dn["stderr"]})
     g1 = line.get("gmrf_config1")
     if g1 is not None:
         cfg = workloads.CONFIGS[1]
@@ -875,20 +880,26 @@ def reference_errors(line):
 
 
 def dense_leg(args, torch):
-    """Dense kernel-matrix path (tensor cores): a d = 32768 BF16 SPD matrix
-    (2.1 GB), n = 30, M = 32.  The step streams B once: bytes per step =
-    2 d^2 + 12 d M (vectors); the MMA work is 3 x 2 d^2 M (three BF16 parts)."""
+    """Dense kernel-matrix path (tensor cores): the Kac-Murdock-Szego matrix
+    A_ik = 0.5^|i-k| at d = 32768 in BF16 (2.1 GB; 0.5^k is exact in BF16 down
+    to the 1e-40 range, the rest rounds to 0), n = 30, M = 32, on its known
+    spectral interval [1/3, 3].  Its exact logdet is (d - 1) log(0.75)
+    (added by the CPU-baseline block).  The step streams B once: bytes per
+    step = 2 d^2 + 12 d M (vectors); the MMA work is 3 x 2 d^2 M (three BF16
+    parts of w_j)."""
     from paper_1503_06394_gb300 import DenseLogdet
 
-    d, n, M = args.d or 32768, args.n or 30, 32
-    g = torch.Generator(device="cuda").manual_seed(1005)
-    A = (torch.rand((d, d), device="cuda", generator=g) * 2 - 1) * (0.5 / d)
-    A = (A + A.T) / 2
-    A.fill_diagonal_(1.0)
-    Ab = A.to(torch.bfloat16)
-    del A
+    d, n, M, rho = args.d or 32768, args.n or 30, 32, 0.5
+    Ab = torch.empty((d, d), dtype=torch.bfloat16, device="cuda")
+    cols = torch.arange(d, device="cuda", dtype=torch.float32)
+    for r0 in range(0, d, 2048):
+        rows = torch.arange(r0, min(d, r0 + 2048), device="cuda", dtype=torch.float32)
+        Ab[r0:r0 + rows.numel()] = torch.pow(rho, (rows[:, None] - cols[None, :]).abs()).to(torch.bfloat16)
+    del cols
     m = DenseLogdet(Ab, d)
-    a, b = m.auto_interval(0)
+    # eigenvalues of rho^|i-k| lie in ((1 - rho)/(1 + rho), (1 + rho)/(1 - rho))
+    a, b = (1 - rho) / (1 + rho), (1 + rho) / (1 - rho)
+    m.set_interval(a, b)
     m.estimate(n, M, 0)
     steps = max(1, args.steps)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -905,9 +916,9 @@ def dense_leg(args, torch):
     peak, src = read_peaks()
     step_bytes = 2 * d * d + 12 * d * M
     gbs = n * step_bytes / (ms / 1e3) / 1e9
-    return {"workload": "dense SPD, BF16, d=%d (uniform off-diagonals, unit diagonal), n=%d, M=%d" % (d, n, M),
-            "interval": [a, b], "ms_per_estimate": ms, "gbs": gbs, "pct_of_peak": 100 * gbs / peak,
-            "tensor_tflops": n * 3 * 2 * d * d * M / (ms / 1e3) / 1e12, "logdet": r["logdet"],
+    return {"workload": "dense Kac-Murdock-Szego matrix 0.5^|i-k|, BF16, d=%d, n=%d, M=%d" % (d, n, M),
+            "d": d, "rho": rho, "interval": [a, b], "ms_per_estimate": ms, "gbs": gbs, "pct_of_peak": 100 * gbs / peak,
+            "tensor_tflops": n * 3 * 2 * d * d * M / (ms / 1e3) / 1e12, "logdet": r["logdet"], "stderr": r["stderr"],
             "kernel": "dense_step_kernel (tcgen05.mma kind::f16, TMA, TMEM)"}
 
 

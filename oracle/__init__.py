@@ -9,6 +9,8 @@ The arithmetic lives in ``oracle.c`` (plain C, FP64, OpenMP over rows); this
 module compiles it on first use, wraps it with ctypes, and adds the closed-form
 exact references that are easiest to state in numpy:
 
+* ``kms_logdet`` -- log det of the Kac-Murdock-Szego matrix rho^|i-k|,
+  (d - 1) log(1 - rho^2).
 * ``grid_laplacian_logdet`` -- log det(kappa^2 I + L) for the 5-point Dirichlet
   Laplacian on an N x N grid, from its separable eigenvalues
   kappa^2 + 4 sin^2(pi i / (2(N+1))) + 4 sin^2(pi j / (2(N+1))).
@@ -281,6 +283,19 @@ def grid_laplacian_logdet(N: int, kappa2: float) -> float:
     s = 4.0 * np.sin(np.pi * np.arange(1, N + 1) / (2.0 * (N + 1))) ** 2
     lam = kappa2 + s[:, None] + s[None, :]
     return math.fsum(np.log(lam).ravel().tolist())
+
+
+def kms_logdet(d: int, rho: float) -> float:
+    """log det of the d x d Kac-Murdock-Szego matrix A_ik = rho^|i-k|, |rho| < 1.
+
+    With white noise e, x_0 = e_0 and x_i = rho x_{i-1} + sqrt(1 - rho^2) e_i
+    has covariance rho^|i-k|; x = L e for a lower triangular L whose diagonal
+    is 1, sqrt(1 - rho^2), ..., sqrt(1 - rho^2), so A = L L^T and
+    det A = (1 - rho^2)^(d-1)."""
+    import math
+    if d <= 0:
+        return 0.0
+    return (d - 1) * math.log1p(-rho * rho)
 
 
 def chebyshev_error_bound(delta: float, n: int) -> float:

@@ -114,14 +114,32 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // ------------------------------------------------------------------ the step
 template <int P>
 struct DenseSmem {
-    // ring depth: 3 at P = 32 leaves room for two CTAs per SM (104 KB each),
-    // so one CTA's epilogue overlaps another's main loop; 4 at P = 64; 2 at 128
+    // ring depth: 3 at P = 32 leaves room for two CTAs per SM (85 KB each),
+    // so one CTA's epilogue overlaps another's main loop (4 stages, 113 KB,
+    // measured 35 % slower); 4 at P = 64; 2 at 128
     static constexpr int kStages = P == 32 ? 3 : P == 64 ? 4 : 2;
     static constexpr int kA = kDRows * kDK * 2;        // 16 KB
     static constexpr int kX = kDSplit * P * kDK * 2;   // 3 parts x P rows x 128 B
     static constexpr int kStage = kA + kX;
-    static constexpr int kBytes = kStage * kStages + 1024 /*align*/ + 256 /*barriers*/ +
-                                  kDRows * (P + 1) * 4 /*moment transpose*/;
+    // the epilogue reuses the ring once every MMA has completed: the moment
+    // transpose [128][P+1] and, per warp, a 32 x 33 tile for its rows of
+    // w_j, w_{j-1} and w_{j+1} (coalesced loads and stores)
+    // The i-th K block a CTA takes goes to TMEM accumulator i mod kAcc; the
+    // kAcc accumulators are added in FP32 (round to nearest) in the epilogue.
+    // The tensor cores' accumulation rounds each addition in a way that does
+    // not average out: the error grows with the additions into one accumulator
+    // that follow a large term (it showed as a probe-independent moment bias,
+    // logdet -1.15 instead of about -0.02 for a near-identity d = 32768
+    // matrix, -0.31 with 4 accumulators, -0.10 with 16).  So each CTA also
+    // takes its K blocks starting after its diagonal block, which comes last:
+    // the large diagonal products meet few later additions.  (16 accumulators
+    // need 512 TMEM columns, one CTA per SM: 35 % slower.)
+    static constexpr int kAcc = 4;
+    static constexpr uint32_t kTmemCols = (uint32_t)(kAcc * P);  // 128, 256 or 512
+    static constexpr int kTr = kDRows * (P + 1) * 4;
+    static constexpr int kTile = 32 * 33 * 4;
+    static_assert(kTr + 2 * (kDThreads / 32) * kTile <= kStage * kStages, "epilogue buffers must fit the ring");
+    static constexpr int kBytes = kStage * kStages + 1024 /*align*/ + 256 /*barriers*/;
     static_assert(kBytes <= 232448, "shared memory");
 };
 
@@ -136,9 +154,12 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned ring (swizzle atoms)
     uint8_t* gbase = smem_raw + (base - raw);
     const uint32_t bars = base + S::kStage * kDStages;  // full[S], empty[S], accum
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + S::kStage * kDStages + 9 * 8);
-    int* fail = reinterpret_cast<int*>(gbase + S::kStage * kDStages + 9 * 8 + 4);
-    float* tr = reinterpret_cast<float*>(gbase + S::kStage * kDStages + 256);  // [128][P+1]
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (2 * kDStages + 1) * 8 + S::kStage * kDStages);
+    int* fail = reinterpret_cast<int*>(gbase + (2 * kDStages + 1) * 8 + 4 + S::kStage * kDStages);
+    // epilogue buffers in the ring (valid once the accumulator is complete)
+    float* tr = reinterpret_cast<float*>(gbase);  // [128][P+1]
+    float* tile_own = reinterpret_cast<float*>(gbase + S::kTr + (threadIdx.x >> 5) * 2 * S::kTile);  // [32][33]
+    float* tile_prev = tile_own + 32 * 33;
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (kDStages + s); };
     const uint32_t accum = bars + 8u * (2 * kDStages);
@@ -158,7 +179,7 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
     }
     if (warp == 0) {  // TMEM: P FP32 columns x 128 lanes
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"((uint32_t)P));
+                     "r"(S::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -168,7 +189,10 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
     int issued = 0;  // producer: stages loaded
 
     if (warp == 0 && lane == 0) {
-        // producer: TMA into the ring
+        // producer: TMA into the ring; the i-th block taken is K block
+        // (kfirst + i) mod nk, so that the diagonal blocks (columns row0 ..
+        // row0 + 127) come last
+        const int kfirst = (int)(((row0 + kDRows) / kDK) % nk);
         for (int kb = 0; kb < nk; ++kb) {
             const int s = kb % kDStages;
             if (kb >= kDStages && !mbar_wait(empty(s), ((kb / kDStages) - 1) & 1)) {
@@ -177,9 +201,10 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
             }
             mbar_expect_tx(full(s), S::kStage);
             const uint32_t sa = base + S::kStage * s;
-            tma_load_2d(sa, &tmA, full(s), kb * kDK, (int)row0);
+            const int kx = (kfirst + kb) % nk;  // K block of this stage
+            tma_load_2d(sa, &tmA, full(s), kx * kDK, (int)row0);
             for (int q = 0; q < kDSplit; ++q)
-                tma_load_2d(sa + S::kA + q * P * kDK * 2, &tmX, full(s), kb * kDK, q * P);
+                tma_load_2d(sa + S::kA + q * P * kDK * 2, &tmX, full(s), kx * kDK, q * P);
             issued = kb + 1;
         }
     } else if (warp == 1 && lane == 0) {
@@ -199,7 +224,9 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
 #pragma unroll
                 for (int q = 0; q < kDSplit; ++q) {
                     const uint64_t bd = smem_desc_sw128(sa + S::kA + q * P * kDK * 2 + kk * 32);
-                    umma_bf16(tmem, ad, bd, idesc, (kb | kk | q) != 0);
+                    // accumulator kb mod kAcc; its first MMA overwrites
+                    umma_bf16(tmem + (uint32_t)((kb % S::kAcc) * P), ad, bd, idesc,
+                              (kb >= S::kAcc || kk != 0 || q != 0) ? 1u : 0u);
                 }
             }
             umma_commit(empty(s));
@@ -217,10 +244,29 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
         const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
         const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
         constexpr int NW = P <= 32 ? 1 : P / 32;
-#pragma unroll
+        // this warp's rows rw .. rw + nr - 1 (thread lane holds row rw + lane)
+        const int64_t rw = row0 + warp * 32;
+        const int nr = (int)(args.d - rw < 32 ? (args.d - rw > 0 ? args.d - rw : 0) : 32);
+#pragma unroll 1
         for (int c0 = 0; c0 < P; c0 += 32) {
             float acc[32];
             tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
+            // the other accumulators, added in a fixed order (those that never
+            // received an MMA, when nk < kAcc, are skipped)
+#pragma unroll 1
+            for (int a = 1; a < S::kAcc && a < nk; ++a) {
+                float part[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * P + c0), part);
+#pragma unroll
+                for (int q = 0; q < 32; ++q) acc[q] += part[q];
+            }
+            // columns c0 .. c0 + 31 of w_j and w_{j-1} for the warp's rows, one
+            // 128-byte row at a time
+            for (int r = 0; r < nr; ++r) {
+                if (PREV != 0) tile_own[r * 33 + lane] = __ldg(args.own + (rw + r) * P + c0 + lane);
+                if (PREV == 2) tile_prev[r * 33 + lane] = __ldg(args.wprev + (rw + r) * P + c0 + lane);
+            }
+            __syncwarp();
             if (live) {
                 const uint32_t word = __ldg(args.vbits + row * NW + c0 / 32);
 #pragma unroll
@@ -228,12 +274,12 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
                     const int p = c0 + q;
                     const float vm = p < args.mreal ? 1.f : 0.f;
                     const float v = vm * __uint_as_float(0x3f800000u | (((word >> q) & 1u) << 31));
-                    const float own = PREV == 0 ? v : __ldg(args.own + row * P + p);
+                    const float own = PREV == 0 ? v : tile_own[lane * 33 + q];
                     float y = fmaf(scale, acc[q], -shift * own) + fmaf(scale_lo, acc[q], -shift_lo * own);
                     float w;
                     if (PREV == 0) w = y;
-                    else w = fmaf(2.f, y, -(PREV == 1 ? v : __ldg(args.wprev + row * P + p)));
-                    args.out[row * P + p] = w;
+                    else w = fmaf(2.f, y, -(PREV == 1 ? v : tile_prev[lane * 33 + q]));
+                    tile_own[lane * 33 + q] = w;  // w_{j+1}, stored below by rows
                     const __nv_bfloat16 hi = __float2bfloat16_rn(w);
                     const float r1 = w - __bfloat162float(hi);
                     const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
@@ -247,6 +293,9 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
 #pragma unroll
                 for (int q = 0; q < 32; ++q) tr[threadIdx.x * (P + 1) + c0 + q] = 0.f;
             }
+            __syncwarp();
+            for (int r = 0; r < nr; ++r) args.out[(rw + r) * P + c0 + lane] = tile_own[r * 33 + lane];
+            __syncwarp();
         }
     } else {
         if (threadIdx.x == 0) atomicOr(args.err, 1u);
@@ -268,7 +317,7 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
     __syncthreads();
     if (warp == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)P));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
     }
 }
 

@@ -15,14 +15,16 @@ def torch():
     return require_gpu()
 
 
-def dense_spd_bf16(d, seed, density=1.0):
+def dense_spd_bf16(d, seed, density=1.0, margin=1.0):
     """Symmetric, diagonally dominant dense matrix rounded to BF16 (uint16 bits)
-    and its FP64 upcast."""
+    and its FP64 upcast; the diagonal is margin x the absolute off-diagonal row
+    sum + 1 (a margin above 1 keeps the Gershgorin discs of the BF16 values
+    positive when d is large)."""
     rng = np.random.default_rng(seed)
     A = rng.uniform(-1.0, 1.0, size=(d, d)) * (rng.random((d, d)) < density)
     A = (A + A.T) / 2
     np.fill_diagonal(A, 0.0)
-    A[np.diag_indices(d)] = np.abs(A).sum(axis=1) + 1.0
+    A[np.diag_indices(d)] = margin * np.abs(A).sum(axis=1) + 1.0
     A /= A.diagonal().max() * 2
     bits = A.astype(np.float32).view(np.uint32).astype(np.uint64)
     b16 = ((bits + 0x7FFF + ((bits >> 16) & 1)) >> 16).astype(np.uint16)
@@ -112,3 +114,30 @@ def test_dense_matches_csr_path(torch):
     rs = m.estimate(30, 32, 1)
     m.close()
     assert abs(rd["logdet"] - rs["logdet"]) <= 1e-5 * abs(rs["logdet"])
+
+
+def test_dense_multi_tile_sampled(torch):
+    """d = 8192: 64 row tiles of 128 and 128 K-blocks of 64 per tile, so the TMA
+    ring wraps many times and every CTA's accumulator sums many MMAs.  Every
+    moment of probes 0, 17 and 31 against the oracle on the same BF16 values
+    stored as CSR, and those probes' Gamma_p within 1e-5."""
+    d, n, M, seed = 8192, 12, 32, 5
+    b16, A = dense_spd_bf16(d, 123, margin=1.1)
+    rowptr, col, val = csr_of(A)
+    del A
+    lo, hi = oracle.gershgorin(rowptr, col, val)
+    from paper_1503_06394_gb300 import DenseLogdet
+
+    m = DenseLogdet(b16, d)
+    m.set_interval(lo, hi)
+    r = m.estimate(n, M, seed, moments=True, details=True)
+    m.close()
+    probes = [0, 17, 31]
+    ref = oracle.estimate(rowptr, col, val, lo, hi, n, M, seed=seed, probes=probes)
+    dt = np.abs(r["t"][:, probes] - ref["t"])
+    tol = moment_tol(d, n, row_terms=d)
+    rel = [abs(r["gamma_p"][p] - ref["gamma_p"][q]) / abs(ref["gamma_p"][q]) for q, p in enumerate(probes)]
+    print("dense d=%d: max |dt|/tol %.3g, Gamma_p rel err %s, moment errors j=1: %s" % (
+        d, (dt / tol).max(), ["%.2e" % x for x in rel], dt[1]))
+    assert np.all(dt <= tol), (dt / tol).max()
+    assert max(rel) <= 1e-5

@@ -224,6 +224,21 @@ def test_grid_closed_form(oracle_mod):
     assert abs(oracle_mod.grid_laplacian_logdet(g["N"], g["kappa2"]) - g["logdet"]) < 1e-6
 
 
+def test_kms_closed_form(oracle_mod):
+    """log det of rho^|i-k| against numpy's slogdet, and its spectrum inside
+    [(1 - |rho|)/(1 + |rho|), (1 + |rho|)/(1 - |rho|)] (the interval the dense
+    benchmark gives the estimator)."""
+    for d in (1, 2, 5, 64, 300):
+        for rho in (0.5, -0.3, 0.9, 0.0):
+            i = np.arange(d)
+            A = rho ** np.abs(i[:, None] - i[None, :]).astype(np.float64)
+            ld = np.linalg.slogdet(A)[1]
+            assert abs(oracle_mod.kms_logdet(d, rho) - ld) < 1e-10 * max(1.0, abs(ld)), (d, rho)
+            ev = np.linalg.eigvalsh(A)
+            r = abs(rho)
+            assert ev[0] >= (1 - r) / (1 + r) * (1 - 1e-12) and ev[-1] <= (1 + r) / (1 - r) * (1 + 1e-12)
+
+
 def test_alg1_literal_equals_interval_form(oracle_mod):
     """Algorithm 1 as printed (recurrence on (I-2B)/(1-2 delta), coefficients of
     log(1-((1-2 delta)x+1)/2)) equals the [delta, 1-delta] interval form."""
