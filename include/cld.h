@@ -318,7 +318,9 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *      variant 5 runs; tiles with more than 16 stored entries per row on
  *      average read their indices and values from global memory.  Its waits
  *      are bounded: cld_estimate / cld_grad return CLD_ERR_TIMEOUT if one
- *      gave up (results invalid).  Single matrices only (batches: 0 to 5).
+ *      gave up (results invalid).  Batch handles have a staged tile-queue
+ *      form (queue tiles cut into sub-tiles of 2048 / P rows), and
+ *      cld_batch_estimate returns CLD_ERR_TIMEOUT the same way.
  * The default at creation is 6 from d = 1e5 up; below, 3 when the matrix
  * holds at most 6 stored entries per row on average, else 4 (batches: 0).
  * The variant also sets the grid size, so the last bits of the moments (their
@@ -327,7 +329,8 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
 CLD_API cld_status cld_set_kernel_variant(cld_handle h, int variant);
 
 /* Autotuner (no paper counterpart): times three blocks of `reps` launches of
- * the general recurrence step of every variant on this matrix with M probes,
+ * the general recurrence step of every variant on this matrix with M probes
+ * (for CLD_GENERAL both kernels of a step: y = C w_j and the step on C^T y),
  * each candidate scored by its fastest block (workspace and interval must be set;
  * the workspace contents are overwritten) and keeps the fastest on the handle
  * (the current choice stays unless another is at least 2 % faster).  On a

@@ -318,22 +318,40 @@ __global__ void __launch_bounds__(kThreads, 3) adjoint_kernel_wide(const AdjArgs
 // global memory, and write H and lambda_i back to global memory.  MODE 1..3
 // (MODE 0 has no gathers and runs the wide form).
 template <int MP, typename VT, int MODE, class C>
-struct AdjStagedLayout {
+struct AdjStagedSizes {
     using G = StagedGeom<MP, C::NC>;
     static constexpr bool kW = MODE != 3;       // w_i rows (MODE 3 uses v)
     static constexpr bool kOwn = MODE != 3;     // lambda_{i+1} rows
     static constexpr bool kPrev = MODE == 2;    // lambda_{i+2} rows
+    static constexpr int rp_bytes = staged_up16((G::T + 2) * 8);
+    // indices, H accumulators and values of capr entries a row, then the rows
+    static constexpr int stage_of(int capr) {
+        return staged_up16(rp_bytes + 2 * staged_up16(capr * G::T * 4) + staged_up16(capr * G::T * (int)sizeof(VT)) +
+                           ((kW ? 1 : 0) + (kOwn ? 1 : 0) + (kPrev ? 1 : 0)) * G::T * MP * 4 +
+                           staged_up16(G::T * G::NW * 4));
+    }
+    static constexpr int static_of(int) { return 512; }
+};
+
+template <int MP, typename VT, int MODE, class C>
+struct AdjStagedLayout {
+    using G = StagedGeom<MP, C::NC>;
+    using Z = AdjStagedSizes<MP, VT, MODE, C>;
+    using R = StagedRing<Z, C>;
+    static constexpr bool kW = Z::kW, kOwn = Z::kOwn, kPrev = Z::kPrev;
+    static constexpr int CAP = R::capr * G::T;  // stored entries a stage holds
     static constexpr int rp = 0;
-    static constexpr int col = rp + staged_up16((G::T + 2) * 8);
-    static constexpr int h = col + staged_up16(G::CAP * 4);
-    static constexpr int val = h + staged_up16(G::CAP * 4);
-    static constexpr int w = val + staged_up16(G::CAP * (int)sizeof(VT));
+    static constexpr int col = rp + Z::rp_bytes;
+    static constexpr int h = col + staged_up16(CAP * 4);
+    static constexpr int val = h + staged_up16(CAP * 4);
+    static constexpr int w = val + staged_up16(CAP * (int)sizeof(VT));
     static constexpr int own = w + (kW ? G::T * MP * 4 : 0);
     static constexpr int prev = own + (kOwn ? G::T * MP * 4 : 0);
     static constexpr int sg = prev + (kPrev ? G::T * MP * 4 : 0);
     static constexpr int stage = staged_up16(sg + staged_up16(G::T * G::NW * 4));
-    static constexpr int NS = C::budget / stage >= 4 ? 4 : C::budget / stage >= 3 ? 3 : 2;
+    static constexpr int NS = R::ns;
     static constexpr int bytes = NS * stage;
+    static_assert(stage == Z::stage_of(R::capr), "stage regions and stage_of disagree");
 };
 
 template <int MP, typename VT, int MODE, class C>
@@ -375,7 +393,7 @@ __global__ void __launch_bounds__(C::threads, C::MINB) adjoint_kernel_staged(con
         const int64_t nnz = __ldg(rowptr + d);
         staged_producer_loop<NS, T>(lane, mine, d, rowptr, args.withhold_tile, args.err, bars,
                                     [&](int s, uint32_t bar, int64_t r0, int rows, int64_t k0, int64_t k1) {
-            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, bar, r0, rows, d, k0, k1, nnz, G::CAP, rowptr,
+            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, bar, r0, rows, 0, d, k0, k1, nnz, S::CAP, rowptr,
                                          args.col, val, args.H, S::kW ? args.w : nullptr,
                                          S::kOwn ? args.lam_in : nullptr, S::kPrev ? args.lam_prev : nullptr,
                                          args.vbits, S::rp, S::col, S::val, S::h, S::w, S::own, S::prev, S::sg,
@@ -545,7 +563,7 @@ static cudaError_t launch_adj_staged_one(int grid, cudaStream_t s, const AdjArgs
     using C = AdjStagedCfg;
     constexpr auto kern = adjoint_kernel_staged<MP, VT, MODE, C>;
     constexpr int smem = AdjStagedLayout<MP, VT, MODE, C>::bytes;
-    cudaError_t e = smem_opt_in<kern>(smem, 256);
+    cudaError_t e = smem_opt_in<kern>(smem, C::MINB);
     if (e != cudaSuccess || grid == 0) return e;
     return launch_pdl(kern, grid, smem, s, a, C::threads);
 }
@@ -660,7 +678,7 @@ static int adj_ctas_mp(int form) {
             using C = AdjStagedCfg;
             constexpr auto kern = adjoint_kernel_staged<MP, VT, 2, C>;
             constexpr int smem = AdjStagedLayout<MP, VT, 2, C>::bytes;
-            e = smem_opt_in<kern>(smem, 256);
+            e = smem_opt_in<kern>(smem, C::MINB);
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::threads, smem);
         } else {
             e = form == 1

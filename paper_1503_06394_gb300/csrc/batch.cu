@@ -10,6 +10,7 @@
 // block's tiles in tile order.
 #include <math.h>
 
+#include "step_staged.cuh"
 #include "step_wide.cuh"
 
 namespace cld {
@@ -215,6 +216,280 @@ static cudaError_t launch_batch_wide(StepKind kind, int grid, cudaStream_t s, co
     }
 }
 
+// The tile-queue step with staged tiles (variant 6 for batches): the CTA's
+// queue tiles (tile blockIdx.x, then every gridDim.x-th) are cut into
+// sub-tiles of T = 2048 / P rows, which the producer warp stages into the
+// ring as step_kernel_staged does (the copies of row-indexed arrays start up
+// to 3 rows early, at a multiple of 4, since tiles start where blocks do);
+// the consumer warps compute them with 8 probes per lane and the block's own
+// interval.  Each queue tile's moments are folded per warp into one of NS + 1
+// shared slots; the warp that arrives last (a shared counter) sums the slot
+// over the warps in a fixed order into the tile's partials, so no consumer
+// ever waits for another (a stalled wait cannot hang the CTA), and a slot is
+// reused only NS + 1 tiles later, when every warp is past that tile.
+template <int MP, typename VT, int GATHER, int PREV, class C>
+__global__ void __launch_bounds__(C::threads, C::MINB) batch_step_kernel_staged(const BatchStepArgs ba) {
+    static_assert(MP >= 8, "staged tiles need at least 8 probes per panel");
+    using G = StagedGeom<MP, C::NC>;
+    using S = StagedLayout<MP, VT, PREV, 1, C, true>;
+    constexpr int PPL = G::PPL, LPR = G::LPR, RPW = G::RPW, T = G::T, NW = G::NW, NS = S::NS;
+    constexpr int U = C::U, NC = C::NC, NSLOT = NS + 1;
+    constexpr bool kMask = GATHER == 1 || PREV != 2;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2 * NS];
+    __shared__ int64_t hdr_kc[NS], hdr_kv[NS];
+    __shared__ int hdr_staged[NS];
+    __shared__ double red[NSLOT][NC][MP];
+    __shared__ int red_cnt[NSLOT];
+
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    auto full = [&](int s) { return smem_u32(&bars[s]); };
+    auto empty = [&](int s) { return smem_u32(&bars[NS + s]); };
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(full(s), 32);
+            mbar_init(empty(s), NC);
+        }
+        for (int k = 0; k < NSLOT; ++k) red_cnt[k] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    pdl_wait();  // w_j, w_{j-1}, the signs, tiles and parameters come from earlier kernels
+    // No early trigger: the next kernel's CTAs are placed when this one ends,
+    // on SMs whose shared-memory carveout can then follow that kernel's
+    // (placed early, they run with this kernel's carveout and its smaller L1).
+
+    const StepArgs& args = ba.s;
+    const int64_t d = args.d;
+    const VT* __restrict__ val = static_cast<const VT*>(args.val);
+    const int64_t* __restrict__ rowptr = args.rowptr;
+
+    if (warp == NC) {
+        // ------------------------------------------------------------ producer
+        const int64_t nnz = __ldg(rowptr + d);
+        int64_t t = blockIdx.x;
+        Tile tl{};
+        int64_t r0 = 0, k0 = 0, k1 = 0;
+        auto rows_at = [&](int64_t r) { return (int)(tl.hi - r < T ? tl.hi - r : T); };
+        if (t < ba.ntiles) {
+            tl = ba.tiles[t];
+            r0 = tl.lo;
+            k0 = __ldg(rowptr + r0);
+            k1 = __ldg(rowptr + r0 + rows_at(r0));
+        }
+        int64_t it = 0;
+        bool ok = true;
+        while (t < ba.ntiles) {
+            const int s = (int)(it % NS);
+            const int64_t use = it / NS;
+            if (use >= 1 && !__all_sync(0xffffffffu, mbar_wait(empty(s), (uint32_t)((use + 1) & 1)))) {
+                ok = false;
+                break;
+            }
+            const int rows = rows_at(r0);
+            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, full(s), r0, rows, (int)(r0 & 3), d, k0, k1, nnz,
+                                         S::CAP, rowptr, args.col, val, nullptr, PREV != 0 ? args.own : nullptr,
+                                         PREV == 2 ? args.wprev : nullptr, nullptr, args.vbits, S::rp, S::col,
+                                         S::val, -1, S::own, S::prev, -1, S::sg, hdr_kc[s], hdr_kv[s],
+                                         hdr_staged[s]);
+            ++it;
+            // the next sub-tile (of this queue tile, or the CTA's next one) and
+            // its entry bounds, loaded while the stage fills
+            r0 += T;
+            if (r0 >= tl.hi) {
+                t += gridDim.x;
+                if (t >= ba.ntiles) break;
+                tl = ba.tiles[t];
+                r0 = tl.lo;
+            }
+            k0 = __ldg(rowptr + r0);
+            k1 = __ldg(rowptr + r0 + rows_at(r0));
+        }
+        if (!ok) {
+            if (lane == 0) atomicOr(args.err, 1u);
+            for (int64_t j = it > NS ? it - NS : 0; j < it; ++j)
+                mbar_wait(full((int)(j % NS)), (uint32_t)((j / NS) & 1));
+        }
+    } else {
+        // ------------------------------------------------------------ consumers
+        const int sub = lane % LPR;
+        const int g_in_w = lane / LPR;
+        const int lr = warp * RPW + g_in_w;  // this lane's row within a sub-tile
+        const int q0 = sub * PPL;
+        const int wsel = q0 >> 5, bsh = q0 & 31;
+        float mk[PPL];
+#pragma unroll
+        for (int q = 0; q < PPL; ++q) mk[q] = (!kMask || q0 + q < args.mreal) ? 1.f : 0.f;
+        const int64_t kend = value_end<VT>(rowptr, d);
+        int64_t it = 0, qt = 0;  // sub-tiles and queue tiles taken
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ba.ntiles && ok; t += gridDim.x, ++qt) {
+            const Tile tl = ba.tiles[t];
+            const Params* P = ba.bprm + tl.blk;
+            const float scale = P->scale_hi, scale_lo = P->scale_lo, shift = P->shift_hi, shift_lo = P->shift_lo;
+            float tacc[PPL];
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) tacc[q] = 0.f;
+            for (int64_t r0 = tl.lo; r0 < tl.hi; r0 += T, ++it) {
+                const int s = (int)(it % NS);
+                if (!__all_sync(0xffffffffu, mbar_wait(full(s), (uint32_t)((it / NS) & 1)))) {
+                    if (lane == 0) atomicOr(args.err, 2u);
+                    ok = false;
+                    break;
+                }
+                const int rows = (int)(tl.hi - r0 < T ? tl.hi - r0 : T);
+                const int pre = (int)(r0 & 3);
+                const unsigned char* st = smem + s * S::stage;
+                if (lr < rows) {
+                    const int sl = pre + lr;  // staged row
+                    const int64_t* rp = reinterpret_cast<const int64_t*>(st + S::rp);
+                    const int64_t k0 = rp[sl], k1 = rp[sl + 1];
+                    float acc[PPL];
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) acc[q] = 0.f;
+                    auto consume = [&](const int (&c)[U], const uint32_t (&ab)[U]) {
+                        float xv[U][PPL];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            if (c[u] >= 0) {
+                                if (GATHER == 1)
+                                    signs8(__ldg(args.vbits + (int64_t)c[u] * NW + wsel), bsh, mk, xv[u]);
+                                else
+                                    ldg8(args.x + (int64_t)c[u] * MP + q0, xv[u]);
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < PPL; ++q) xv[u][q] = 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const float a = __uint_as_float(ab[u]);
+#pragma unroll
+                            for (int q = 0; q < PPL; ++q) acc[q] = fmaf(a, xv[u][q], acc[q]);
+                        }
+                    };
+                    if (hdr_staged[s]) {
+                        const int32_t* cs = reinterpret_cast<const int32_t*>(st + S::col);
+                        const VT* vs = reinterpret_cast<const VT*>(st + S::val);
+                        const int e0 = (int)(k0 - hdr_kc[s]), e1 = (int)(k1 - hdr_kc[s]);
+                        const int dv = (int)(hdr_kc[s] - hdr_kv[s]);
+                        for (int e = e0; e < e1; e += U) {
+                            int c[U];
+                            uint32_t ab[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const bool okk = e + u < e1;
+                                c[u] = okk ? cs[e + u] : -1;
+                                ab[u] = okk ? smem_val_bits<VT>(vs + e + u + dv) : 0u;
+                            }
+                            consume(c, ab);
+                        }
+                    } else {
+                        const bool edge = std::is_same<VT, bf16_t>::value && (k0 == 0 || k1 == kend);
+                        for (int64_t k = k0; k < k1; k += U) {
+                            int c[U];
+                            uint32_t ab[U];
+#pragma unroll
+                            for (int u = 0; u < U; ++u) {
+                                const bool okk = k + u < k1;
+                                c[u] = okk ? __ldg(args.col + k + u) : -1;
+                                ab[u] = okk ? load_bits(val, k + u, edge) : 0u;
+                            }
+                            consume(c, ab);
+                        }
+                    }
+                    float v[PPL], own[PPL], pv[PPL], res[PPL];
+                    signs8(reinterpret_cast<const uint32_t*>(st + S::sg)[sl * NW + wsel], bsh, mk, v);
+                    if (PREV == 0) {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) own[q] = v[q];
+                    } else {
+                        const float4* o4 = reinterpret_cast<const float4*>(st + S::own + (sl * MP + q0) * 4);
+                        const float4 a = o4[0], b = o4[1];
+                        own[0] = a.x; own[1] = a.y; own[2] = a.z; own[3] = a.w;
+                        own[4] = b.x; own[5] = b.y; own[6] = b.z; own[7] = b.w;
+                    }
+                    if (PREV == 2) {
+                        const float4* p4 = reinterpret_cast<const float4*>(st + S::prev + (sl * MP + q0) * 4);
+                        const float4 a = p4[0], b = p4[1];
+                        pv[0] = a.x; pv[1] = a.y; pv[2] = a.z; pv[3] = a.w;
+                        pv[4] = b.x; pv[5] = b.y; pv[6] = b.z; pv[7] = b.w;
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PPL; ++q) pv[q] = v[q];
+                    }
+#pragma unroll
+                    for (int q = 0; q < PPL; ++q) {
+                        res[q] = recurrence_update1<PREV>(acc[q], own[q], pv[q], scale, scale_lo, shift, shift_lo);
+                        tacc[q] = fmaf(v[q], res[q], tacc[q]);
+                    }
+                    const int64_t row = r0 + lr;
+                    st4(args.out + row * MP + q0, make_float4(res[0], res[1], res[2], res[3]));
+                    st4(args.out + row * MP + q0 + 4, make_float4(res[4], res[5], res[6], res[7]));
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(empty(s));
+            }
+            if (!ok) break;
+            // this warp's share of the tile's moments into slot qt mod NSLOT;
+            // the last warp to arrive sums the slot in warp order
+            const int slot = (int)(qt % NSLOT);
+#pragma unroll
+            for (int q = 0; q < PPL; ++q) {
+                double tq = tacc[q];
+#pragma unroll
+                for (int off = LPR; off < 32; off <<= 1) tq += __shfl_xor_sync(0xffffffffu, tq, off);
+                if (g_in_w == 0) red[slot][warp][q0 + q] = tq;
+            }
+            __syncwarp();
+            __threadfence_block();
+            int last = 0;
+            if (lane == 0) last = atomicAdd(&red_cnt[slot], 1) == NC - 1;
+            last = __shfl_sync(0xffffffffu, last, 0);
+            if (last) {
+                __threadfence_block();
+                for (int p = lane; p < MP; p += 32) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < NC; ++w) sum += red[slot][w][p];
+                    ba.tpart[t * MP + p] = sum;
+                }
+                __syncwarp();
+                if (lane == 0) red_cnt[slot] = 0;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int MP, typename VT, int GATHER, int PREV>
+static cudaError_t launch_one_batch_staged(int grid, cudaStream_t s, const BatchStepArgs& a) {
+    using C = StagedCfg<4, 8, 3>;
+    constexpr auto kern = batch_step_kernel_staged<MP, VT, GATHER, PREV, C>;
+    constexpr int smem = StagedLayout<MP, VT, PREV, 1, C, true>::bytes;
+    cudaError_t e = smem_opt_in<kern>(smem, C::MINB);
+    if (e != cudaSuccess || grid == 0) return e;
+    return launch_pdl(kern, grid, smem, s, a, C::threads);
+}
+
+template <int MP, typename VT>
+static cudaError_t launch_batch_staged(StepKind kind, int grid, cudaStream_t s, const BatchStepArgs& a) {
+    // bulk copies need 16-byte aligned CSR arrays; otherwise the wide lanes
+    const bool aligned = (reinterpret_cast<uintptr_t>(a.s.rowptr) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(a.s.col) % 16 == 0) &&
+                         (reinterpret_cast<uintptr_t>(a.s.val) % 16 == 0);
+    if (!aligned || a.s.err == nullptr) return launch_batch_wide<MP, VT>(kind, grid, s, a);
+    switch (kind) {
+        case kStepFirst: return launch_one_batch_staged<MP, VT, 1, 0>(grid, s, a);
+        case kStepSecond: return launch_one_batch_staged<MP, VT, 0, 1>(grid, s, a);
+        case kStepGeneral: return launch_one_batch_staged<MP, VT, 0, 2>(grid, s, a);
+        case kStepFirstFromFloat: return launch_one_batch_staged<MP, VT, 0, 0>(grid, s, a);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <int MP, typename VT, int GATHER, int PREV, int IMPL>
 static cudaError_t launch_one_batch(int grid, cudaStream_t s, const BatchStepArgs& a) {
     constexpr auto kern = batch_step_kernel<MP, VT, GATHER, PREV, IMPL>;
@@ -246,6 +521,9 @@ static cudaError_t launch_batch_mp(StepKind kind, int grid, cudaStream_t s, cons
         case 5:
             if constexpr (MP >= 8) return launch_batch_wide<MP, VT>(kind, grid, s, a);
             else return launch_batch_impl<MP, VT, 0>(kind, grid, s, a);  // wide lanes need 8 probes
+        case 6:
+            if constexpr (MP >= 8) return launch_batch_staged<MP, VT>(kind, grid, s, a);
+            else return launch_batch_impl<MP, VT, 0>(kind, grid, s, a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -498,6 +498,7 @@ static cld_status enqueue_batch(cld_ctx* h, const Layout& L, int n, int M, uint6
         bs.s.vbits = x.vbits;
         bs.s.mreal = mreal;
         bs.s.impl = h->impl;
+        bs.s.err = x.flags + 1;  // the staged tiles' pipeline error word
         for (int j = 0; j < n; ++j) {
             if (events && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
             const float* wj = j >= 1 ? W[j % 3] : nullptr;
@@ -510,6 +511,7 @@ static cld_status enqueue_batch(cld_ctx* h, const Layout& L, int n, int M, uint6
                 p.d = h->d;
                 p.rowptr = h->rowptr; p.col = h->col; p.val = h->val;
                 p.vbits = x.vbits; p.mreal = mreal; p.impl = h->impl;
+                p.err = bs.s.err;  // the staged form's error word, as the C^T step's
                 p.x = wj; p.out = Y;
                 CUDA_TRY(launch_step(L.panel, (int)h->dtype, j == 0 ? kProdBits : kProdFloat, L.grid, h->stream, p));
                 ++launches;
@@ -1173,6 +1175,8 @@ cld_status cld_batch_estimate(cld_handle h, int n, int M, uint64_t seed, double*
     if (h->ws_bytes < L.total)
         return fail(CLD_ERR_NOMEM, "workspace has %zu bytes, %zu needed", h->ws_bytes, L.total);
     cld_status st;
+    uint32_t* perr = at<uint32_t>(h, L.flags) + 1;
+    if (h->impl == 6) CUDA_TRY(cudaMemsetAsync(perr, 0, 4, h->stream));
     if (h->use_graph) {
         BatchAuxArgs x = batch_aux_args(h, L);
         x.seed = seed;
@@ -1184,6 +1188,8 @@ cld_status cld_batch_estimate(cld_handle h, int n, int M, uint64_t seed, double*
     }
     if (st != CLD_OK) return st;
     std::vector<Result> r((size_t)h->nb);
+    uint32_t perr_h = 0;
+    if (h->impl == 6) CUDA_TRY(cudaMemcpyAsync(&perr_h, perr, 4, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaMemcpyAsync(r.data(), at<Result>(h, L.bres), sizeof(Result) * h->nb, cudaMemcpyDeviceToHost,
                              h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -1196,6 +1202,7 @@ cld_status cld_batch_estimate(cld_handle h, int n, int M, uint64_t seed, double*
             h->last_step_ms += ms;
         }
     }
+    if (perr_h) return fail(CLD_ERR_TIMEOUT, "a staged-step pipeline wait gave up (results invalid)");
     int bad = -1;
     for (int k = 0; k < h->nb; ++k) {
         logdet_out[k] = r[k].logdet;
@@ -1288,7 +1295,21 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
                 ba.tpart = at<double>(h, L.tpart);
                 bgrid = (int)(ba.ntiles < L.grid ? (ba.ntiles > 0 ? ba.ntiles : 1) : L.grid);
             }
+            // general C: a degree step is y = C w_j and then the step on C^T y,
+            // both with the variant under test, so both are timed
+            StepArgs pa = a;
+            if (general) {
+                CUDA_TRY(cudaMemsetAsync(at<float>(h, L.Y), 0, (size_t)h->d * L.panel * 4, h->stream));
+                pa.rowptr = h->rowptr; pa.col = h->col; pa.val = h->val;
+                pa.x = at<float>(h, L.W[1]); pa.out = at<float>(h, L.Y);
+                a.x = pa.out;
+                ba.s.x = pa.out;
+            }
             auto one = [&]() {
+                if (general) {
+                    const cudaError_t pe = launch_step(L.panel, (int)h->dtype, kProdFloat, L.grid, h->stream, pa);
+                    if (pe != cudaSuccess) return pe;
+                }
                 return h->nb > 0 ? launch_batch_step(L.panel, (int)h->dtype, kStepGeneral, bgrid, h->stream, ba)
                                  : launch_step(L.panel, (int)h->dtype, kStepGeneral, L.grid, h->stream, a);
             };

@@ -213,7 +213,7 @@ struct StepArgs {
 };
 
 constexpr int kNumStepImpls = 7;
-constexpr int kNumBatchImpls = 6;  // variants with a batched (tile-queue) form
+constexpr int kNumBatchImpls = 7;  // variants with a batched (tile-queue) form
 
 enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
                 kStepFirstFromFloat = 5 };

@@ -445,22 +445,47 @@ template <int IMPL, int GATHER>
 constexpr int step_smem() { return ring_bytes(IMPL); }
 
 // Opts kernel K into `bytes` of dynamic shared memory on the current device,
-// once per device (the attribute is per device; ordinals >= 64 set it on
-// every call).  Needed when the dynamic and static shared memory together
-// pass 48 KB (`static_bytes`: the kernel's static shared memory, an upper
-// bound is enough), before the first launch or occupancy query.
+// once per device (the attributes are per device; ordinals >= 64 set them on
+// every call), before the first launch or occupancy query.  Needed when the
+// dynamic and static shared memory together pass 48 KB; the static size is
+// read from the kernel's attributes.  With `ctas` > 0 it also asks for the
+// smallest shared-memory carveout that holds `ctas` CTAs per SM (dynamic +
+// static + the per-CTA reservation each; fewer if the SM cannot hold that
+// many): left to itself the driver may take a smaller one (more L1, or room
+// for a kernel launched early beside it), and a kernel whose grid assumes
+// `ctas` resident CTAs per SM then runs in 1.5 waves.
 template <auto K>
-cudaError_t smem_opt_in(int bytes, int static_bytes = 0) {
-    if (bytes + static_bytes <= 48 * 1024) return cudaSuccess;
+cudaError_t smem_opt_in(int bytes, int ctas = 0) {
+    if (ctas == 0 && bytes <= 48 * 1024) return cudaSuccess;
     static std::atomic<unsigned long long> done{0};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
     if (bit != 0 && (done.load(std::memory_order_acquire) & bit) != 0) return cudaSuccess;
-    e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess && bit != 0) done.fetch_or(bit, std::memory_order_acq_rel);
-    return e;
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, K);
+    if (e != cudaSuccess) return e;
+    const long long stat = (long long)fa.sharedSizeBytes;
+    if (bytes + stat > 48 * 1024) {
+        e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+        if (e != cudaSuccess) return e;
+    }
+    if (ctas > 0) {
+        int per_sm = 0, reserved = 0;
+        e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        if (e != cudaSuccess) return e;
+        const long long per_cta = bytes + stat + reserved;
+        long long want = ctas;  // as many of `ctas` as the SM can hold
+        while (want > 1 && want * per_cta > per_sm) --want;
+        long long pct = per_sm > 0 ? (100 * want * per_cta + per_sm - 1) / per_sm : 100;
+        if (pct > 100) pct = 100;
+        e = cudaFuncSetAttribute(K, cudaFuncAttributePreferredSharedMemoryCarveout, (int)pct);
+        if (e != cudaSuccess) return e;
+    }
+    if (bit != 0) done.fetch_or(bit, std::memory_order_acq_rel);
+    return cudaSuccess;
 }
 
 template <int MP, typename VT, int GATHER, int PREV, int EPI, int IMPL>

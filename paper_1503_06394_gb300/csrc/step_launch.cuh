@@ -52,7 +52,7 @@ cudaError_t launch_one_staged(int grid, cudaStream_t s, const StepArgs& a) {
         if (!aligned || a.err == nullptr) return launch_one_wide<MP, VT, GATHER, PREV, EPI>(grid, s, a);
         constexpr auto kern = step_kernel_staged<MP, VT, GATHER, PREV, EPI, C>;
         constexpr int smem = StagedLayout<MP, VT, PREV, EPI, C>::bytes;
-        cudaError_t e = smem_opt_in<kern>(smem, kStagedStaticBytes<MP, C::NC>);
+        cudaError_t e = smem_opt_in<kern>(smem, C::MINB);
         if (e != cudaSuccess || grid == 0) return e;
         return launch_pdl(kern, grid, smem, s, a, C::threads);
     } else {
@@ -153,7 +153,7 @@ int ctas_per_sm_staged() {
         using C = typename StagedShape<I>::C;
         constexpr auto kern = step_kernel_staged<MP, VT, 0, 2, 1, C>;
         constexpr int smem = StagedLayout<MP, VT, 2, 1, C>::bytes;
-        if (smem_opt_in<kern>(smem, kStagedStaticBytes<MP, C::NC>) != cudaSuccess) return 1;
+        if (smem_opt_in<kern>(smem, C::MINB) != cudaSuccess) return 1;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::threads, smem) != cudaSuccess) return 1;
         return n > 0 ? n : 1;
     } else {

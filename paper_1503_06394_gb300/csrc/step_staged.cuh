@@ -24,8 +24,9 @@
 //   32-byte gather: slower, the L1 data path being the busiest unit.)
 //
 // A tile whose entries do not fit the stage (more than 16 per row on
-// average) is staged without its indices and values, which the consumers
-// then read from global memory.  Bulk copies need 16-byte aligned addresses
+// average; 12 for the shapes whose stages are cut to keep L1, StagedRing) is
+// staged without its indices and values, which the consumers then read from
+// global memory.  Bulk copies need 16-byte aligned addresses
 // and sizes: the index and value ranges are widened to 16-byte boundaries
 // (neighbouring rows' entries, never read), and the bytes that would pass
 // the end of the row-pointer, index or value array are copied by plain loads
@@ -51,9 +52,12 @@ struct StagedCfg {
     static constexpr int NC = NC_;
     static constexpr int MINB = MINB_;
     static constexpr int threads = 32 * (NC + 1);
-    // shared memory a CTA may take for its ring (the rest of the SM's 227 KB
-    // stays L1 for the gathers, which need it)
-    static constexpr int budget = MINB >= 3 ? 66 * 1024 : MINB == 2 ? 84 * 1024 : 120 * 1024;
+    // Shared memory (ring and static) one CTA may hold: MINB CTAs, with the
+    // 1 KB the runtime reserves for each, fit the 196 KB shared-memory
+    // carveout, so the SM keeps 60 KB of L1 for the gathers' lines in flight.
+    // The next carveout (228 KB, 28 KB of L1) halved the speed of a batched
+    // general step whose gathers miss L1.
+    static constexpr int cta_bytes = 196 * 1024 / MINB - 1024;
 };
 
 template <int MP, int NC>
@@ -63,34 +67,65 @@ struct StagedGeom {
     static constexpr int RPW = 32 / LPR;               // rows per consumer warp
     static constexpr int T = NC * RPW;                 // rows per tile (256 NC / MP)
     static constexpr int NW = MP <= 32 ? 1 : MP / 32;  // sign words per row
-    static constexpr int CAP = 16 * T;                 // stored entries a stage holds
 };
 
 __host__ __device__ constexpr int staged_up16(int x) { return (x + 15) / 16 * 16; }
 
-// Upper bound of the kernel's static shared memory (moment partials,
-// barriers, stage headers): counted against the 48 KB default limit.
-template <int MP, int NC>
-constexpr int kStagedStaticBytes = NC * MP * 8 + 256;
+// Ring shape from a stage's size at a given entry capacity (`stage_of(capr)`:
+// bytes of one stage holding capr stored entries a row) and the static shared
+// memory at a given stage count (`static_of(ns)`, an upper bound): 16 entries a
+// row if two stages fit the CTA's share, else 12 if two stages fit, else 16
+// (the CTA then takes more than its share and the SM holds fewer CTAs or less
+// L1); then as many stages (2 to 4) as fit.  Tiles with more entries than the
+// capacity read their indices and values from global memory.
+template <class L, class C>
+struct StagedRing {
+    static constexpr bool fits(int capr, int ns) { return ns * L::stage_of(capr) + L::static_of(ns) <= C::cta_bytes; }
+    static constexpr int capr = fits(16, 2) ? 16 : fits(12, 2) ? 12 : 16;
+    static constexpr int ns = fits(capr, 4) ? 4 : fits(capr, 3) ? 3 : 2;
+};
 
-// Byte offsets of one stage's regions, the stages of the ring and the dynamic
-// shared memory.
-template <int MP, typename VT, int PREV, int EPI, class C>
-struct StagedLayout {
+// Sizes of the forward step's stage (at a given entry capacity) and static
+// shared memory (at a given stage count).  BATCH: the tile-queue kernel, whose
+// stages hold 3 rows beyond the tile's T (its copies start up to 3 rows early
+// to sit on 16-byte boundaries) and whose static memory holds NS + 1 moment
+// slots.
+template <int MP, typename VT, int PREV, int EPI, class C, bool BATCH>
+struct StagedSizes {
     using G = StagedGeom<MP, C::NC>;
+    static constexpr int TR = G::T + (BATCH ? 3 : 0);  // rows a stage holds
     static constexpr bool kOwn = EPI == 1 && PREV != 0;
     static constexpr bool kPrev = EPI == 1 && PREV == 2;
     static constexpr bool kSigns = EPI == 1;
-    static constexpr int rp = 0;                                          // T + 2 row pointers
-    static constexpr int col = rp + staged_up16((G::T + 2) * 8);          // CAP indices
-    static constexpr int val = col + staged_up16(G::CAP * 4);             // CAP values
-    static constexpr int own = val + staged_up16(G::CAP * (int)sizeof(VT));
-    static constexpr int prev = own + (kOwn ? G::T * MP * 4 : 0);         // T x P floats each
-    static constexpr int sg = prev + (kPrev ? G::T * MP * 4 : 0);         // T x NW sign words
-    static constexpr int stage = staged_up16(sg + (kSigns ? staged_up16(G::T * G::NW * 4) : 0));
-    // stages in the ring: as many as fit the budget, 2 to 4
-    static constexpr int NS = C::budget / stage >= 4 ? 4 : C::budget / stage >= 3 ? 3 : 2;
+    static constexpr int rp_bytes = staged_up16((TR + 2) * 8);  // TR + 2 row pointers
+    static constexpr int stage_of(int capr) {
+        return staged_up16(rp_bytes + staged_up16(capr * G::T * 4) + staged_up16(capr * G::T * (int)sizeof(VT)) +
+                           (kOwn ? TR * MP * 4 : 0) + (kPrev ? TR * MP * 4 : 0) +
+                           (kSigns ? staged_up16(TR * G::NW * 4) : 0));
+    }
+    static constexpr int static_of(int ns) { return (kSigns ? (BATCH ? ns + 1 : 1) * C::NC * MP * 8 : 0) + 512; }
+};
+
+// Byte offsets of one stage's regions, the stages of the ring and the dynamic
+// shared memory.
+template <int MP, typename VT, int PREV, int EPI, class C, bool BATCH = false>
+struct StagedLayout {
+    using G = StagedGeom<MP, C::NC>;
+    using Z = StagedSizes<MP, VT, PREV, EPI, C, BATCH>;
+    using R = StagedRing<Z, C>;
+    static constexpr int TR = Z::TR;
+    static constexpr bool kOwn = Z::kOwn, kPrev = Z::kPrev, kSigns = Z::kSigns;
+    static constexpr int CAP = R::capr * G::T;                            // stored entries a stage holds
+    static constexpr int rp = 0;
+    static constexpr int col = rp + Z::rp_bytes;                          // CAP indices
+    static constexpr int val = col + staged_up16(CAP * 4);                // CAP values
+    static constexpr int own = val + staged_up16(CAP * (int)sizeof(VT));
+    static constexpr int prev = own + (kOwn ? TR * MP * 4 : 0);           // TR x P floats each
+    static constexpr int sg = prev + (kPrev ? TR * MP * 4 : 0);           // TR x NW sign words
+    static constexpr int stage = staged_up16(sg + (kSigns ? staged_up16(TR * G::NW * 4) : 0));
+    static constexpr int NS = R::ns;
     static constexpr int bytes = NS * stage;
+    static_assert(stage == Z::stage_of(R::capr), "stage regions and stage_of disagree");
 };
 
 template <typename VT>
@@ -109,26 +144,30 @@ __device__ __forceinline__ uint32_t smem_val_bits<bf16_t>(const bf16_t* p) {
 }
 
 // Bounds and copies of one tile for the producer warp: row pointers
-// r0 .. r0 + rows, the stored indices and values of entries [k0, k1) (and, with
-// H, the per-entry FP32 accumulators of the same range), up to three blocks of
-// `rows` x MP floats starting at row r0, and the rows' sign words, into the
-// stage at `st` (byte offsets o_*; a null source or a negative offset: not
-// staged).  Lane 0 registers the bytes on the stage's mbarrier and issues the
+// r0 - pre .. r0 + rows, the stored indices and values of entries [k0, k1)
+// (and, with H, the per-entry FP32 accumulators of the same range), up to
+// three blocks of `pre + rows` x MP floats starting at row r0 - pre, and those
+// rows' sign words, into the stage at `st` (byte offsets o_*; a null source
+// or a negative offset: not staged).  pre (0 .. 3) puts row-indexed copies on
+// 16-byte boundaries when r0 is not a multiple of 4 (batch tiles); the pre
+// rows are copied, never used.  Lane 0 registers the bytes on the stage's mbarrier and issues the
 // bulk copies; lanes 1 .. 15 copy what the bulk copies must leave out at the
 // ends of the arrays; every lane then arrives once (the barrier expects 32).
 // The index range is widened to 16-byte boundaries; if it holds more than
 // cap entries, indices, values and H stay in global memory (hdr_staged = 0).
 template <int MP, int NW, typename VT>
 __device__ __forceinline__ void staged_fill_tile(int lane, unsigned char* st, uint32_t bar, int64_t r0, int rows,
-                                                 int64_t d, int64_t k0, int64_t k1, int64_t nnz, int cap,
+                                                 int pre, int64_t d, int64_t k0, int64_t k1, int64_t nnz, int cap,
                                                  const int64_t* rowptr, const int32_t* col, const VT* val,
                                                  const float* H, const float* v0, const float* v1, const float* v2,
                                                  const uint32_t* vbits, int o_rp, int o_col, int o_val, int o_h,
                                                  int o_v0, int o_v1, int o_v2, int o_sg, int64_t& hdr_kc,
                                                  int64_t& hdr_kv, int& hdr_staged) {
     constexpr int UV = 16 / (int)sizeof(VT);  // values per 16 bytes
-    // row pointers r0 .. r0 + rows
-    uint32_t rp_bulk = (uint32_t)(rows + 1) * 8u;
+    const int64_t ra = r0 - pre;  // first staged row
+    const int nrow = rows + pre;  // staged rows
+    // row pointers ra .. r0 + rows
+    uint32_t rp_bulk = (uint32_t)(nrow + 1) * 8u;
     bool rp_tail = false;
     if (rp_bulk & 15u) {
         if (r0 + rows + 1 <= d) {
@@ -147,8 +186,8 @@ __device__ __forceinline__ void staged_fill_tile(int lane, unsigned char* st, ui
     const uint32_t col_bytes = staged ? (uint32_t)(kzb - ka) * 4u : 0u;
     const uint32_t h_bytes = H != nullptr ? col_bytes : 0u;
     const uint32_t val_bytes = staged ? (uint32_t)(kvzb - kva) * (uint32_t)sizeof(VT) : 0u;
-    const uint32_t vec_bytes = (uint32_t)rows * MP * 4u;
-    const uint32_t sg_bytes = o_sg >= 0 ? (uint32_t)staged_up16(rows * NW * 4) : 0u;
+    const uint32_t vec_bytes = (uint32_t)nrow * MP * 4u;
+    const uint32_t sg_bytes = o_sg >= 0 ? (uint32_t)staged_up16(nrow * NW * 4) : 0u;
     if (lane == 0) {
         hdr_kc = ka;
         hdr_kv = kva;
@@ -156,16 +195,16 @@ __device__ __forceinline__ void staged_fill_tile(int lane, unsigned char* st, ui
         const uint32_t tx = rp_bulk + col_bytes + h_bytes + val_bytes + (v0 ? vec_bytes : 0u) +
                             (v1 ? vec_bytes : 0u) + (v2 ? vec_bytes : 0u) + sg_bytes;
         mbar_expect_tx(bar, tx);
-        bulk_g2s(smem_u32(st + o_rp), rowptr + r0, rp_bulk, bar);
+        bulk_g2s(smem_u32(st + o_rp), rowptr + ra, rp_bulk, bar);
         if (col_bytes) bulk_g2s(smem_u32(st + o_col), col + ka, col_bytes, bar);
         if (h_bytes) bulk_g2s(smem_u32(st + o_h), H + ka, h_bytes, bar);
         if (val_bytes) bulk_g2s(smem_u32(st + o_val), val + kva, val_bytes, bar);
-        if (v0) bulk_g2s(smem_u32(st + o_v0), v0 + r0 * MP, vec_bytes, bar);
-        if (v1) bulk_g2s(smem_u32(st + o_v1), v1 + r0 * MP, vec_bytes, bar);
-        if (v2) bulk_g2s(smem_u32(st + o_v2), v2 + r0 * MP, vec_bytes, bar);
-        if (sg_bytes) bulk_g2s(smem_u32(st + o_sg), vbits + r0 * NW, sg_bytes, bar);
+        if (v0) bulk_g2s(smem_u32(st + o_v0), v0 + ra * MP, vec_bytes, bar);
+        if (v1) bulk_g2s(smem_u32(st + o_v1), v1 + ra * MP, vec_bytes, bar);
+        if (v2) bulk_g2s(smem_u32(st + o_v2), v2 + ra * MP, vec_bytes, bar);
+        if (sg_bytes) bulk_g2s(smem_u32(st + o_sg), vbits + ra * NW, sg_bytes, bar);
     } else {
-        if (lane == 1 && rp_tail) reinterpret_cast<int64_t*>(st + o_rp)[rows] = __ldg(rowptr + r0 + rows);
+        if (lane == 1 && rp_tail) reinterpret_cast<int64_t*>(st + o_rp)[nrow] = __ldg(rowptr + r0 + rows);
         if (staged && lane >= 2 && lane < 6) {
             const int64_t e = kzb + (lane - 2);
             if (e < k1) {
@@ -269,7 +308,9 @@ __global__ void __launch_bounds__(C::threads, C::MINB) step_kernel_staged(const 
     }
     __syncthreads();
     pdl_wait();  // w_j, w_{j-1}, the signs and the parameters come from earlier kernels
-    pdl_trigger();
+    // No early trigger: the next kernel's CTAs are placed when this one ends,
+    // with their own shared-memory carveout (batched general steps alternate
+    // this kernel with the batched C^T step, whose carveout differs).
 
     const int64_t d = args.d;
     const int64_t ntiles = (d + T - 1) / T;
@@ -282,7 +323,7 @@ __global__ void __launch_bounds__(C::threads, C::MINB) step_kernel_staged(const 
         const int64_t nnz = __ldg(rowptr + d);
         staged_producer_loop<NS, T>(lane, mine, d, rowptr, args.withhold_tile, args.err, bars,
                                     [&](int s, uint32_t bar, int64_t r0, int rows, int64_t k0, int64_t k1) {
-            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, bar, r0, rows, d, k0, k1, nnz, G::CAP, rowptr,
+            staged_fill_tile<MP, NW, VT>(lane, smem + s * S::stage, bar, r0, rows, 0, d, k0, k1, nnz, S::CAP, rowptr,
                                          args.col, val, nullptr, S::kOwn ? args.own : nullptr,
                                          S::kPrev ? args.wprev : nullptr, nullptr, args.vbits, S::rp, S::col,
                                          S::val, -1, S::own, S::prev, -1, S::kSigns ? S::sg : -1, hdr_kc[s],
