@@ -971,7 +971,7 @@ def main():
                     default=None,
                     help="run one leg alone (with --d / --n overrides) and print its JSON")
     ap.add_argument("--n", type=int, default=None, help="degree override for --only")
-    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5, 6],
+    ap.add_argument("--variant", type=int, default=None, choices=[0, 1, 2, 3, 4, 5, 6, 7],
                     help="pin the recurrence-step inner-loop variant instead of autotuning it")
     ap.add_argument("--tile-rows", type=int, default=None,
                     help="with --variant and --only batch: rows per work tile of the batched step")

@@ -110,7 +110,9 @@ CLD_API cld_status cld_create_dense(cld_handle* out, int64_t d, int64_t ld, cons
 /* Bytes of device workspace an estimate of degree n with M probes needs
  * (with_grad != 0: also enough for cld_grad).  No paper counterpart
  * (memory infrastructure): the three recurrence blocks w_{j-1}, w_j, w_{j+1}
- * of Algorithm 1 are the dominant term, d x panel x 4 bytes each.
+ * of Algorithm 1 are the dominant term, d x panel x 4 bytes each; CLD_SPD
+ * single-matrix handles add variant 7's gather-window plan (nnz x 4 bytes and
+ * 4 bytes per row).
  * Errors: CLD_ERR_INVALID. */
 CLD_API cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad, size_t* bytes);
 
@@ -320,7 +322,19 @@ CLD_API cld_status cld_set_graph(cld_handle h, int on);
  *      are bounded: cld_estimate / cld_grad return CLD_ERR_TIMEOUT if one
  *      gave up (results invalid).  Batch handles have a staged tile-queue
  *      form (queue tiles cut into sub-tiles of 2048 / P rows), and
- *      cld_batch_estimate returns CLD_ERR_TIMEOUT the same way.
+ *      cld_batch_estimate returns CLD_ERR_TIMEOUT the same way;
+ *   7: gather windows, for CLD_SPD single-matrix handles whose tiles of rows
+ *      reach few compact index ranges (stencils, points numbered by cell):
+ *      a plan, computed on the device once per workspace and panel width,
+ *      gives each tile of 2048 / P rows up to 4 ranges of rows (gaps of up to
+ *      16 rows merged) and each stored entry its row in them; the staged
+ *      tiles of variant 6 then also copy those ranges of w_j, and every
+ *      gather reads shared memory.  Tiles whose columns need more ranges or
+ *      more rows than a stage holds gather from global memory; steps 0, the
+ *      products of CLD_GENERAL handles, panels of fewer than 16 probes and
+ *      FP64 values at 16 probes run variant 6.  Needs the plan's workspace
+ *      (cld_workspace_size counts it for CLD_SPD handles: nnz x 4 bytes and
+ *      4 bytes per row); batch handles do not take it.
  * The default at creation is 6 from d = 1e5 up; below, 3 when the matrix
  * holds at most 6 stored entries per row on average, else 4 (batches: 0).
  * The variant also sets the grid size, so the last bits of the moments (their

@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcld.so")
-SOURCES = ["cld_api.cu", "aux.cu", "spectral.cu", "step_f32.cu", "step_bf16.cu", "step_f64.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "dense.cu"]
+SOURCES = ["cld_api.cu", "aux.cu", "spectral.cu", "step_f32.cu", "step_bf16.cu", "step_f64.cu", "noalloc.cu", "adjoint.cu", "batch.cu", "dense.cu", "window.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -79,6 +79,7 @@ struct cld_ctx {
     int impl = 1;  // recurrence-step inner loop (see step_kernel.cuh)
     int ckpt = 0;  // gradient checkpoint interval K (0: keep every w_j)
     int64_t withhold_tile = 0;  // testing aid of variant 6 (cld_debug_withhold_tile)
+    int plan_panel = 0;         // panel width of variant 7's plan in the workspace (0: none)
 
     // batch (nb > 0): block-diagonal super matrix, blocks [blk_rows[b], blk_rows[b+1])
     int nb = 0;
@@ -116,6 +117,8 @@ struct Layout {
     int nseg, ckK;           // checkpointed gradient: segments of w_1..w_{n-1}, their length K (0: every w_j kept)
     size_t blk_rows, tile_start, tiles, bprm, ab, bres;  // batches
     size_t xt[2];            // dense: BF16 splits of w_j, [3][panel][dx], double-buffered
+    size_t wtab, lcol;       // variant 7's gather-window plan (single-matrix SPD handles)
+    bool plan;
     int64_t dx;
     int panel, nw, grid, ggrid;
 };
@@ -140,7 +143,7 @@ static int panel_for(int M) {
 static int step_grid(const cld_ctx* h, int panel) {
     // rows a CTA covers in one pass: 4 probes per lane (the staged tiles of
     // variant 6: tiles of 2048 / panel rows)
-    const int rows_per_cta = (h->impl == 6 && panel >= 8) ? 2048 / panel : (kThreads / 32) * (128 / panel);
+    const int rows_per_cta = (h->impl >= 6 && panel >= 8) ? 2048 / panel : (kThreads / 32) * (128 / panel);
     const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
     const int64_t full = (int64_t)step_ctas_per_sm(panel, (int)h->dtype, h->impl) * h->sms;
     int64_t g = need < full ? need : full;
@@ -165,6 +168,13 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
         L.colT = o; o += align_up((size_t)h->nnz * 4);
         L.valT = o; o += align_up((size_t)h->nnz * value_size(h->dtype));
         L.tscratch = o; o += align_up((size_t)(h->d + 1) * 8);
+    }
+    // variant 7's plan: a table row per tile (tiles of 16 or more rows) and
+    // each entry's window row
+    L.plan = h->kind == CLD_SPD && h->nb == 0 && !h->dense;
+    if (L.plan) {
+        L.wtab = o; o += align_up((size_t)((h->d + 15) / 16 + 1) * kWinTabInts * 4);
+        L.lcol = o; o += align_up((size_t)h->nnz * 4);
     }
     const int nprob = h->nb > 0 ? h->nb : 1;
     if (h->nb > 0) {
@@ -279,6 +289,10 @@ static cld_status enqueue_steps(cld_ctx* h, const Layout& L, int n, int M, int p
     a.impl = h->impl;
     a.err = at<uint32_t>(h, L.flags) + 1;
     a.withhold_tile = h->withhold_tile;
+    if (h->impl == 7 && L.plan && h->plan_panel == L.panel) {
+        a.lcol = at<int32_t>(h, L.lcol);
+        a.wtab = at<int32_t>(h, L.wtab);
+    }
     for (int j = j0; j < j1; ++j) {
         // w_{j+1} <- step j; w_j and w_{j-1} from the previous steps (w_0 = v).
         if (events && h->profiling && j == 2) CUDA_TRY(cudaEventRecord(h->ev[2 * pk], h->stream));
@@ -565,6 +579,20 @@ static cld_status apply_bintervals(cld_ctx* h, const Layout& L) {
     return CLD_OK;
 }
 
+// Variant 7's gather-window plan for the layout's panel width, computed on
+// the handle's stream before the steps that read it (once per workspace and
+// panel width; an estimate at another width recomputes it, so a graph
+// captured at this width never reads another width's plan).
+static cld_status ensure_plan(cld_ctx* h, const Layout& L) {
+    if (h->impl != 7 || !L.plan || h->d == 0 || h->plan_panel == L.panel) return CLD_OK;
+    const int capx = window_capx(L.panel, (int)h->dtype);
+    if (capx <= 0) return CLD_OK;  // no windows at this panel width: variant 6 runs
+    CUDA_TRY(launch_window_plan(L.panel, h->rowptr, h->col, h->d, capx, at<int32_t>(h, L.wtab),
+                                at<int32_t>(h, L.lcol), h->sms, h->stream));
+    h->plan_panel = L.panel;
+    return CLD_OK;
+}
+
 // Runs enqueue(with_seed = false) through a CUDA graph captured once per
 // (call kind, n, M, variant, workspace, tile size); the seed is set by a
 // separate launch before the graph.
@@ -706,6 +734,7 @@ cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes) {
     h->ws = static_cast<char*>(dev_ptr);
     h->ws_bytes = bytes;
     h->ready = false;
+    h->plan_panel = 0;
     uint32_t* flags = at<uint32_t>(h, L.flags);
     CUDA_TRY(cudaMemsetAsync(flags, 0, 256, h->stream));
     if (h->d > 0 && !h->dense)
@@ -821,9 +850,10 @@ cld_status cld_estimate(cld_handle h, int n, int M, uint64_t seed, double* logde
         h->last_total_launches = h->last_step_launches = 0;
         return CLD_OK;
     }
-    cld_status st;
+    cld_status st = ensure_plan(h, L);
+    if (st != CLD_OK) return st;
     uint32_t* err = at<uint32_t>(h, L.flags) + 1;
-    const bool pipelined = h->dense || h->impl == 6;  // kernels with bounded pipeline waits
+    const bool pipelined = h->dense || h->impl >= 6;  // kernels with bounded pipeline waits
     if (pipelined) CUDA_TRY(cudaMemsetAsync(err, 0, 4, h->stream));
     auto body = [&](bool with_seed) {
         return h->dense ? enqueue_dense(h, L, n, M, seed, with_seed) : enqueue_estimate(h, L, n, M, seed, with_seed);
@@ -888,6 +918,8 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
     int launches = 0, step_launches = 0;
     cld_status st = ensure_events(h, M);
     if (st != CLD_OK) return st;
+    st = ensure_plan(h, L);
+    if (st != CLD_OK) return st;
     CUDA_TRY(cudaMemsetAsync(flags, 0, 8, h->stream));  // flags and the pipeline error word
     CUDA_TRY(cudaMemsetAsync(H, 0, (size_t)h->nnz * 4, h->stream));
     CUDA_TRY(launch_set_seed(prm, seed, h->stream));
@@ -916,7 +948,7 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         // the reverse step follows the forward's form: per-lane, wide lanes
         // (variant 5) or staged tiles (variant 6; both cover 2048 / panel rows
         // per CTA pass)
-        const int form = L.panel < 8 ? 0 : h->impl == 6 ? 2 : h->impl == 5 ? 1 : 0;
+        const int form = L.panel < 8 ? 0 : h->impl >= 6 ? 2 : h->impl == 5 ? 1 : 0;
         const int rows_per_cta = (kThreads / 32) * ((form > 0 ? 256 : 128) / L.panel);
         const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;
         const int64_t full = (int64_t)adjoint_ctas_per_sm(L.panel, (int)h->dtype, form) * h->sms;
@@ -1275,6 +1307,18 @@ cld_status cld_autotune(cld_handle h, int M, int reps, int* variant_out, float* 
             a.mreal = M < L.panel ? M : L.panel;
             a.impl = v;
             a.err = at<uint32_t>(h, L.flags) + 1;
+            if (v == 7 && L.plan) {
+                const cld_status pst = ensure_plan(h, L);
+                if (pst != CLD_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return pst;
+                }
+                if (h->plan_panel == L.panel) {
+                    a.lcol = at<int32_t>(h, L.lcol);
+                    a.wtab = at<int32_t>(h, L.wtab);
+                }
+            }
             const bool general = h->kind == CLD_GENERAL;
             a.rowptr = general ? at<int64_t>(h, L.rowptrT) : h->rowptr;
             a.col = general ? at<int32_t>(h, L.colT) : h->col;
@@ -1396,11 +1440,11 @@ cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row
     const Layout L = make_layout(h, 1, M, 0);
     if (panel) *panel = L.panel;
     // 4 probes per lane; 8 with the wide lanes (variant 5, panels of 8 or more)
-    const bool wide = (h->impl == 5 || h->impl == 6) && h->nb == 0 && L.panel >= 8;
+    const bool wide = h->impl >= 5 && h->nb == 0 && L.panel >= 8;
     if (lanes_per_row) *lanes_per_row = wide ? L.panel / 8 : L.panel / 4;
     if (ctas) *ctas = L.grid;
-    // variant 6: 8 consumer warps and one producer warp
-    if (threads) *threads = (h->impl == 6 && h->nb == 0 && L.panel >= 8) ? 288 : kThreads;
+    // variants 6 and 7: 8 consumer warps and one producer warp
+    if (threads) *threads = (h->impl >= 6 && h->nb == 0 && L.panel >= 8) ? 288 : kThreads;
     return CLD_OK;
 }
 

@@ -210,9 +210,11 @@ struct StepArgs {
     int impl;                // inner-loop variant (0..kNumStepImpls-1, see step_kernel.cuh)
     uint32_t* err;           // variant 6: set (bits) when a pipeline wait gave up
     int64_t withhold_tile;   // variant 6 testing aid: tile index + 1 never staged (0: none)
+    const int32_t* lcol;     // variant 7: entries' window rows (null: no plan)
+    const int32_t* wtab;     // variant 7: per-tile window ranges
 };
 
-constexpr int kNumStepImpls = 7;
+constexpr int kNumStepImpls = 8;
 constexpr int kNumBatchImpls = 7;  // variants with a batched (tile-queue) form
 
 enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3, kProdFloat = 4,
@@ -223,6 +225,14 @@ enum StepKind { kStepFirst = 0, kStepSecond = 1, kStepGeneral = 2, kProdBits = 3
 // on the current device (done before a stream capture).
 cudaError_t launch_step(int panel, int dtype, StepKind kind, int grid, cudaStream_t stream,
                         const StepArgs& a);
+constexpr int kWinTabInts = 16;  // ints per tile in variant 7's plan table
+
+// Variant 7's gather-window plan (window.cu): one table row per tile of
+// 2048 / panel rows and each entry's window row; window_capx gives the rows a
+// window holds for a panel and value type (0: no windows at that panel).
+cudaError_t launch_window_plan(int panel, const int64_t* rowptr, const int32_t* col, int64_t d, int capx,
+                               int32_t* tab, int32_t* lcol, int sms, cudaStream_t s);
+int window_capx(int panel, int dtype);
 // Resident CTAs per SM of the general step kernel (for grid sizing).
 int step_ctas_per_sm(int panel, int dtype, int impl);
 // Number of sign words per row for a panel width.

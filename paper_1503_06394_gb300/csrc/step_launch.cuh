@@ -6,6 +6,7 @@
 
 #include "step_kernel.cuh"
 #include "step_staged.cuh"
+#include "step_window.cuh"
 #include "step_wide.cuh"
 
 namespace cld {
@@ -60,9 +61,43 @@ cudaError_t launch_one_staged(int grid, cudaStream_t s, const StepArgs& a) {
     }
 }
 
+// Variant 7's step j >= 1 of an SPD matrix (x = w_j): the windowed kernel
+// when the handle's plan for this panel is attached and the arrays are
+// 16-byte aligned, else the staged tiles.  grid 0 opts both kernels in.
+template <int MP, typename VT, int PREV>
+cudaError_t launch_one_window(int grid, cudaStream_t s, const StepArgs& a) {
+    if constexpr (window_ok<MP, VT>()) {
+        using C = WindowShape;
+        constexpr auto kern = step_kernel_window<MP, VT, PREV, C>;
+        constexpr int smem = WindowLayout<MP, VT, PREV, C>::bytes;
+        if (grid == 0) {
+            const cudaError_t e = smem_opt_in<kern>(smem, C::MINB);
+            if (e != cudaSuccess) return e;
+        } else {
+            const bool aligned = (reinterpret_cast<uintptr_t>(a.rowptr) % 16 == 0) &&
+                                 (reinterpret_cast<uintptr_t>(a.lcol) % 16 == 0) &&
+                                 (reinterpret_cast<uintptr_t>(a.col) % 16 == 0) &&
+                                 (reinterpret_cast<uintptr_t>(a.val) % 16 == 0);
+            if (a.lcol != nullptr && a.wtab != nullptr && a.err != nullptr && a.x == a.own && aligned) {
+                const cudaError_t e = smem_opt_in<kern>(smem, C::MINB);
+                if (e != cudaSuccess) return e;
+                return launch_pdl(kern, grid, smem, s, a, C::threads);
+            }
+        }
+    }
+    return launch_one_staged<MP, VT, 0, PREV, 1, 0>(grid, s, a);
+}
+
 template <int MP, typename VT, int IMPL>
 cudaError_t launch_step_impl(StepKind kind, int grid, cudaStream_t s, const StepArgs& a) {
-    if constexpr (IMPL >= 6) {
+    if constexpr (IMPL == 7) {
+        switch (kind) {
+            case kStepSecond: return launch_one_window<MP, VT, 1>(grid, s, a);
+            case kStepGeneral: return launch_one_window<MP, VT, 2>(grid, s, a);
+            default: return launch_step_impl<MP, VT, 6>(kind, grid, s, a);
+        }
+    }
+    if constexpr (IMPL == 6) {
         constexpr int I = IMPL - 6;
         switch (kind) {
             case kStepFirst: return launch_one_staged<MP, VT, 1, 0, 1, I>(grid, s, a);
@@ -106,6 +141,7 @@ cudaError_t launch_step_mp(StepKind kind, int grid, cudaStream_t s, const StepAr
         case 4: return launch_step_impl<MP, VT, 4>(kind, grid, s, a);
         case 5: return launch_step_impl<MP, VT, 5>(kind, grid, s, a);
         case 6: return launch_step_impl<MP, VT, 6>(kind, grid, s, a);
+        case 7: return launch_step_impl<MP, VT, 7>(kind, grid, s, a);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -162,6 +198,21 @@ int ctas_per_sm_staged() {
 }
 
 template <int MP, typename VT>
+int ctas_per_sm_window() {
+    if constexpr (window_ok<MP, VT>()) {
+        using C = WindowShape;
+        constexpr auto kern = step_kernel_window<MP, VT, 2, C>;
+        constexpr int smem = WindowLayout<MP, VT, 2, C>::bytes;
+        int n = 0;
+        if (smem_opt_in<kern>(smem, C::MINB) != cudaSuccess) return 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, C::threads, smem) != cudaSuccess) return 1;
+        return n > 0 ? n : 1;
+    } else {
+        return ctas_per_sm_staged<MP, VT, 0>();
+    }
+}
+
+template <int MP, typename VT>
 int ctas_per_sm_mp(int impl) {
     switch (impl) {
         case 0: return ctas_per_sm_impl<MP, VT, 0>();
@@ -171,6 +222,7 @@ int ctas_per_sm_mp(int impl) {
         case 4: return ctas_per_sm_impl<MP, VT, 4>();
         case 5: return ctas_per_sm_wide<MP, VT>();
         case 6: return ctas_per_sm_staged<MP, VT, 0>();
+        case 7: return ctas_per_sm_window<MP, VT>();
         default: return 1;
     }
 }

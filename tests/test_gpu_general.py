@@ -44,7 +44,7 @@ def test_general_matches_oracle(torch, d, M, n):
     m.close()
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 def test_general_kernel_variants(torch, variant):
     """Algorithm 2's two products per step (C x, then C^T y with the recurrence)
     with every inner-loop variant, including the ring's plain-product form."""

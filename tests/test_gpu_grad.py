@@ -35,9 +35,9 @@ def gpu_grad(B, vals, a, b, n, M, seed, dtype="f32", variant=None):
     return g, G.cpu().numpy().astype(np.float64), r["logdet"]
 
 
-def wendland_small(d=2048, seed=5, sigma2=0.1):
+def wendland_small(d=2048, seed=5, sigma2=0.1, order="random"):
     ell = 0.002 * np.sqrt(1e6 / d)  # same expected neighbour count as the d = 1e6 workload
-    P, _ = workloads.wendland_pattern(d, ell, seed)
+    P, _ = workloads.wendland_pattern(d, ell, seed, order)
     rows = np.repeat(np.arange(d), np.diff(P.rowptr))
     diag = rows == P.col
     return P, diag, ell, sigma2
@@ -64,13 +64,14 @@ def test_grad_matches_oracle_adjoint(torch, kind, n, M):
     assert g == est  # cld_grad's Gamma is the forward estimate
 
 
-@pytest.mark.parametrize("variant", [None, 6])
+@pytest.mark.parametrize("variant", [None, 6, 7])
 @pytest.mark.parametrize("n,K", [(2, 2), (3, 2), (9, 2), (9, 4), (30, 6), (30, 29), (30, 40), (60, 11)])
 def test_grad_checkpointed_equals_store_all(torch, n, K, variant):
     """The checkpointed reverse pass (pairs every K steps, segments recomputed)
     gives bit-identical gradients and estimate to keeping every w_j, with a
-    smaller workspace when n is large (default inner loop, and the staged
-    tiles of variant 6 in both passes)."""
+    smaller workspace when n is large (default inner loop, the staged tiles of
+    variant 6 in both passes, and variant 7's gather windows in the forward
+    steps and their recomputed segments)."""
     from paper_1503_06394_gb300 import CsrLogdet
 
     P, diag, ell, s2 = wendland_small(1024)
@@ -108,19 +109,21 @@ def test_grad_checkpoint_rejects_bad_interval(torch):
     m.close()
 
 
-@pytest.mark.parametrize("variant", [5, 6])
-@pytest.mark.parametrize("kind", ["random", "wendland"])
+@pytest.mark.parametrize("variant", [5, 6, 7])
+@pytest.mark.parametrize("kind", ["random", "wendland", "wendland_cell"])
 @pytest.mark.parametrize("n,M", [(2, 8), (7, 16), (30, 32), (20, 64), (5, 128), (8, 140), (6, 12)])
 def test_grad_wide_lanes_matches_oracle_adjoint(torch, kind, n, M, variant):
-    """With the forward's wide lanes (variant 5) or staged tiles (variant 6)
-    the reverse pass runs its wide form (8 probes per lane, P >= 8; 1 lane per
-    row at P = 8)."""
+    """With the forward's wide lanes (variant 5), staged tiles (variant 6) or
+    gather windows (variant 7) the reverse pass runs its wide or staged form
+    (8 probes per lane, P >= 8; 1 lane per row at P = 8)."""
     if kind == "random":
         B = workloads.sparse_random_spd(1500, 3, 31)
         v32, v64 = B.stored("f32")
         a, b = oracle.gershgorin(B.rowptr, B.col, v64)
     else:
-        P, diag, ell, s2 = wendland_small(1024)
+        # cell order: tiles reach three rows of cells (variant 7's windows)
+        P, diag, ell, s2 = wendland_small(4096 if kind == "wendland_cell" else 1024,
+                                          order="cell" if kind == "wendland_cell" else "random")
         val = workloads.wendland_values(P.val, diag, ell, s2)
         B = workloads.Csr(P.rowptr, P.col, val)
         v32, v64 = B.stored("f32")

@@ -59,7 +59,7 @@ def test_parity_shapes(torch, d, M):
     check(B, "f32", 12, M, seed=d + M)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("M", [3, 8, 16, 32, 64, 128])
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 def test_parity_kernel_variants(torch, variant, M, dtype):
@@ -85,11 +85,11 @@ def test_parity_kernel_variants(torch, variant, M, dtype):
     check(S, dtype, 9, M, seed=M + variant, variant=variant)
 
 
-@pytest.mark.parametrize("variant", [3, 4, 6])
+@pytest.mark.parametrize("variant", [3, 4, 6, 7])
 @pytest.mark.parametrize("M", [16, 64])
 def test_parity_ring_variants_grid(torch, variant, M):
-    """The shared-memory ring variants and the staged tiles on a 64 x 64
-    five-point grid (every row inside the staged chunk, neighbour rows shared
+    """The shared-memory ring variants, the staged tiles and the gather windows
+    on a 64 x 64 five-point grid (every row inside the staged chunk, neighbour rows shared
     between groups) against the oracle."""
     B = workloads.grid_gmrf(64, 0.1)
     r, ref = check(B, "f32", 20, M, seed=M + variant, interval=(0.1, 8.1), variant=variant)
@@ -182,7 +182,7 @@ def test_bf16_storage(torch):
     assert abs(r["logdet"] - ref64["gamma"]) <= 2e-3 * abs(ref64["gamma"])
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7])
 @pytest.mark.parametrize("M", [8, 32, 128])
 def test_bf16_values_at_either_word_half(torch, variant, M):
     """BF16 value arrays that start on a 4-byte boundary or 2 bytes past one,
@@ -191,9 +191,9 @@ def test_bf16_values_at_either_word_half(torch, variant, M):
     hold the array's first or last entry), the other variants 16 bits at a
     time; either way the results must not depend on where the array starts:
     bit-identical across the two starts, and equal to the oracle on the stored
-    values.  (Variant 6 stages only 16-byte aligned arrays: the array 2 bytes
-    past the boundary runs variant 5, whose w_j are the same but whose moment
-    sums run in another order, so there the two starts agree to 1e-5.)"""
+    values.  (Variants 6 and 7 stage only 16-byte aligned arrays: the array 2
+    bytes past the boundary runs variant 5, whose w_j are the same but whose
+    moment sums run in another order, so there the two starts agree to 1e-5.)"""
     from paper_1503_06394_gb300 import CsrLogdet
 
     for d, seed in ((1001, 3), (1000, 4)):  # symmetric pattern + diagonal: nnz has the parity of d
@@ -214,7 +214,7 @@ def test_bf16_values_at_either_word_half(torch, variant, M):
             m.set_interval(a, b)
             runs.append(m.estimate(9, M, M, moments=True))
             m.close()
-        if variant == 6:
+        if variant >= 6:
             assert abs(runs[0]["logdet"] - runs[1]["logdet"]) <= 1e-5 * abs(runs[1]["logdet"])
         else:
             assert runs[0]["logdet"] == runs[1]["logdet"]
@@ -424,7 +424,7 @@ def test_autotune_keeps_parity(torch):
     m = CsrLogdet(B.rowptr, B.col, v32)
     m.set_interval(lo, hi)
     variant, ms = m.autotune(20, 32)
-    assert variant in (0, 1, 2, 3, 4, 5, 6) and ms > 0
+    assert variant in range(8) and ms > 0
     r = m.estimate(20, 32, 1)
     ref = oracle.estimate(B.rowptr, B.col, v64, lo, hi, 20, 32, seed=1)
     assert abs(r["logdet"] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
@@ -460,6 +460,97 @@ def test_parity_staged_tiles(torch, M, dtype, d):
     r6, ref = check(B, dtype, 12, M, seed=M, variant=6)
     r5, _ = check(B, dtype, 12, M, seed=M, variant=5)
     assert abs(r6["logdet"] - r5["logdet"]) <= 1e-6 * abs(r5["logdet"])
+
+
+def windowed_matrices():
+    """Matrices for the gather windows (variant 7): a five-point grid whose
+    tiles reach three row ranges (ragged last tiles at every panel width); a
+    Wendland covariance of points numbered by cell (three rows of cells per
+    tile); the grid with a long-range pair in every 25th row, so tiles that
+    need more than four ranges (no window: global gathers) sit between
+    windowed ones."""
+    G = workloads.grid_gmrf(70, 0.1)
+    W, _ = workloads.wendland(8000, 0.022, 0.1, 31, order="cell")
+    d = G.d
+    rng = np.random.default_rng(5)
+    rows = np.arange(0, d, 25)
+    far = (rows + d // 2 + rng.integers(0, 100, size=rows.size)) % d
+    rr = np.repeat(np.arange(d), np.diff(G.rowptr))
+    Bo = workloads._coo_to_csr(d, np.concatenate([rr, rows, far]), np.concatenate([G.col, far, rows]),
+                               np.concatenate([G.val, np.full(rows.size, -0.5), np.full(rows.size, -0.5)]), "gridfar")
+    R = workloads._abs_row_sums(d, Bo)
+    rrb = np.repeat(np.arange(d), np.diff(Bo.rowptr))
+    Bo.val = np.where(Bo.col == rrb, R[rrb] + 0.1, Bo.val)
+    # Wendland: the kernel is positive semidefinite, so sigma^2 = 0.1 bounds
+    # the spectrum below; the largest absolute row sum bounds it above
+    wb = float(np.max(np.add.reduceat(np.abs(W.val), W.rowptr[:-1])))
+    return {"grid": (G, (0.1, 8.1)), "wendland": (W, (0.1, wb)), "gridfar": (Bo, None)}
+
+
+_WINDOWED = {}
+
+
+@pytest.mark.parametrize("M", [16, 32, 64, 128])
+@pytest.mark.parametrize("dtype", ["f32", "bf16", "f64"])
+@pytest.mark.parametrize("kind", ["grid", "wendland", "gridfar"])
+def test_parity_gather_windows(torch, kind, dtype, M):
+    """Variant 7 (gathers from staged windows of w_j) against the oracle on
+    the three window matrices at every panel width of 16 or more probes and
+    every value type (FP64 at 16 probes has no window room and runs variant 6),
+    and within rounding of variant 6's estimate: the same w_j, moment sums in
+    another CTA order."""
+    if not _WINDOWED:
+        _WINDOWED.update(windowed_matrices())
+    B, interval = _WINDOWED[kind]
+    r7, ref = check(B, dtype, 12, M, seed=M + 1, interval=interval, variant=7)
+    r6, _ = check(B, dtype, 12, M, seed=M + 1, interval=interval, variant=6)
+    assert abs(r7["logdet"] - r6["logdet"]) <= 1e-9 * abs(r6["logdet"])
+    np.testing.assert_allclose(r7["t"], r6["t"], rtol=1e-9, atol=1e-9 * B.d)
+
+
+def test_gather_windows_replan_per_panel(torch):
+    """The window plan depends on the panel width (tiles of 2048 / P rows): one
+    handle estimated at M = 32, then 64, then 32 again through the same CUDA
+    graph, each equal to a fresh handle's estimate at that M."""
+    from paper_1503_06394_gb300 import CsrLogdet
+
+    B = workloads.grid_gmrf(60, 0.1)
+    v32, v64 = B.stored("f32")
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    m.set_kernel_variant(7)
+    m.set_interval(0.1, 8.1)
+    m.set_graph(True)
+    runs = [m.estimate(10, M, 3, moments=True) for M in (32, 64, 32)]
+    m.close()
+    for M, r in zip((32, 64, 32), runs):
+        ref = oracle.estimate(B.rowptr, B.col, v64, 0.1, 8.1, 10, M, seed=3)
+        assert abs(r["logdet"] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
+        dt = np.abs(r["t"] - ref["t"])
+        assert np.all(dt <= moment_tol(B.d, 10))
+    assert runs[0]["logdet"] == runs[2]["logdet"]
+
+
+def test_gather_windows_wait_runs_out(torch):
+    """The bounded waits of variant 7: a withheld tile makes the consumers'
+    waits run out (CLD_ERR_TIMEOUT), and the handle then gives the oracle's
+    result."""
+    from paper_1503_06394_gb300 import CldError, CsrLogdet
+    from paper_1503_06394_gb300 import _binding as Bd
+
+    B = workloads.grid_gmrf(60, 0.1)
+    v32, v64 = B.stored("f32")
+    m = CsrLogdet(B.rowptr, B.col, v32)
+    m.set_kernel_variant(7)
+    m.set_interval(0.1, 8.1)
+    Bd.cld_debug_withhold_tile(m.h, 5)
+    with pytest.raises(CldError) as e:
+        m.estimate(3, 32, 0)
+    assert e.value.status == Bd.CLD_ERR_TIMEOUT
+    Bd.cld_debug_withhold_tile(m.h, 0)
+    r = m.estimate(6, 32, 0)
+    m.close()
+    ref = oracle.estimate(B.rowptr, B.col, v64, 0.1, 8.1, 6, 32, seed=0)
+    assert abs(r["logdet"] - ref["gamma"]) <= 1e-5 * abs(ref["gamma"])
 
 
 def test_staged_wait_runs_out(torch):
