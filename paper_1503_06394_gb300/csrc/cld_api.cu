@@ -946,8 +946,10 @@ cld_status cld_grad(cld_handle h, int n, int M, uint64_t seed, double* logdet_ou
         a.err = flags + 1;
         a.withhold_tile = h->withhold_tile;
         // the reverse step follows the forward's form: per-lane, wide lanes
-        // (variant 5) or staged tiles (variant 6; both cover 2048 / panel rows
-        // per CTA pass)
+        // (variant 5) or staged tiles (variants 6 and 7; a windowed reverse
+        // step measured slower than the staged one: its per-entry SDDMM term
+        // keeps it issue bound, not latency bound; both forms cover 2048 /
+        // panel rows per CTA pass)
         const int form = L.panel < 8 ? 0 : h->impl >= 6 ? 2 : h->impl == 5 ? 1 : 0;
         const int rows_per_cta = (kThreads / 32) * ((form > 0 ? 256 : 128) / L.panel);
         const int64_t need = (h->d + rows_per_cta - 1) / rows_per_cta;

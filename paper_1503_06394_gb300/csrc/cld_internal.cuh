@@ -336,7 +336,7 @@ struct AdjArgs {
 };
 // form: 0 the per-lane reverse step; 1 the wide-lane one (8 probes per lane,
 // panels of at least 8), used when the forward runs variant 5; 2 the staged
-// tiles (variant 6's form; the wide one where it cannot run).
+// tiles (variants 6 and 7; the wide one where it cannot run).
 cudaError_t launch_adjoint(int panel, int dtype, int mode, int grid, cudaStream_t s, const AdjArgs& a, int form);
 int adjoint_ctas_per_sm(int panel, int dtype, int form);
 cudaError_t launch_adjoint_gather(int64_t d, const int64_t* rowptr, const int32_t* col, const float* H,
