@@ -935,8 +935,8 @@ def profiled_traffic(args, B, variant):
     text = open(path).read()
     h = hashlib.sha256()
     # the device code of every variant, its value loads and its grid sizing
-    for name in ("step_kernel.cuh", "step_wide.cuh", "step_staged.cuh", "async_copy.cuh", "cld_internal.cuh",
-                 "step_launch.cuh"):
+    for name in ("step_kernel.cuh", "step_wide.cuh", "step_staged.cuh", "step_window.cuh", "async_copy.cuh",
+                 "cld_internal.cuh", "step_launch.cuh"):
         h.update(open(os.path.join(csrc, name), "rb").read())
     want = h.hexdigest()
     vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())
