@@ -508,6 +508,16 @@ def test_parity_gather_windows(torch, kind, dtype, M):
     np.testing.assert_allclose(r7["t"], r6["t"], rtol=1e-9, atol=1e-9 * B.d)
 
 
+def test_gather_windows_wide_span_falls_back(torch):
+    """d > 65536 random SPD matrix: every tile's columns span more rows than the
+    plan's bitmap covers, so no tile is windowed and variant 7 runs the staged
+    path throughout; the result is the oracle's."""
+    B = workloads.sparse_random_spd(100_000, 3, 41)
+    r7, ref = check(B, "f32", 8, 32, seed=4, variant=7)
+    r6, _ = check(B, "f32", 8, 32, seed=4, variant=6)
+    assert abs(r7["logdet"] - r6["logdet"]) <= 1e-9 * abs(r6["logdet"])
+
+
 def test_gather_windows_replan_per_panel(torch):
     """The window plan depends on the panel width (tiles of 2048 / P rows): one
     handle estimated at M = 32, then 64, then 32 again through the same CUDA
