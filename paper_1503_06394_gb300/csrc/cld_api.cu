@@ -119,6 +119,8 @@ struct Layout {
     size_t xt[2];            // dense: BF16 splits of w_j, [3][panel][dx], double-buffered
     size_t wtab, lcol;       // variant 7's gather-window plan (single-matrix SPD handles)
     bool plan;
+    size_t dpart, dcnt;      // dense: stream-K partial sums [ntiles][dsmax][128][panel], tile counters
+    int dgrid, dsmax;
     int64_t dx;
     int panel, nw, grid, ggrid;
 };
@@ -206,6 +208,12 @@ static Layout make_layout(const cld_ctx* h, int n, int M, int with_grad) {
     if (h->dense) {
         L.dx = (h->d + 63) / 64 * 64;
         for (int i = 0; i < 2; ++i) { L.xt[i] = o; o += align_up((size_t)3 * L.panel * L.dx * 2); }
+        L.dgrid = 1;
+        L.dsmax = 1;
+        if (h->d > 0 && dense_schedule(L.panel, h->d, h->sms, &L.dgrid, &L.dsmax) != cudaSuccess) L.dgrid = 0;
+        const int64_t ntiles = (h->d + 127) / 128;
+        L.dpart = o; o += align_up((size_t)ntiles * L.dsmax * 128 * L.panel * 4);
+        L.dcnt = o; o += align_up((size_t)ntiles * 4);
     }
     // Lanczos scratch (5 FP64 vectors + scalars) reuses the W buffers when they are
     // large enough, else gets its own region.
@@ -358,6 +366,9 @@ static cld_status enqueue_dense(cld_ctx* h, const Layout& L, int n, int M, uint6
         CUDA_TRY(launch_set_seed(prm, seed, h->stream));
         ++launches;
     }
+    if (L.dgrid <= 0) return fail(CLD_ERR_CUDA, "dense step: no launch configuration");
+    // stream-K tile counters start at 0; each step's finishing CTAs reset them
+    CUDA_TRY(cudaMemsetAsync(at<int>(h, L.dcnt), 0, (size_t)((h->d + 127) / 128) * 4, h->stream));
     const int npanels = (M + kMaxPanel - 1) / kMaxPanel;
     for (int pk = 0; pk < npanels; ++pk) {
         const int pbase = pk * kMaxPanel;
@@ -370,7 +381,9 @@ static cld_status enqueue_dense(cld_ctx* h, const Layout& L, int n, int M, uint6
             cudaError_t e = launch_dense_step(L.panel, prev, h->d, h->ld, h->val, xt[j % 2], L.dx,
                                               j >= 1 ? W[j % 3] : nullptr, j >= 2 ? W[(j - 1) % 3] : nullptr,
                                               W[(j + 1) % 3], xt[(j + 1) % 2], vbits,
-                                              tpart + (size_t)j * L.grid * L.panel, prm, mreal, err, h->stream);
+                                              tpart + (size_t)j * L.grid * L.panel, prm, mreal, err,
+                                              at<float>(h, L.dpart), at<int>(h, L.dcnt), L.dsmax, L.dgrid,
+                                              h->stream);
             if (e == cudaErrorNotSupported) return fail(CLD_ERR_UNSUPPORTED, "TMA tensor map encoding unavailable");
             if (e != cudaSuccess) return fail(CLD_ERR_CUDA, "dense step launch: %s", cudaGetErrorString(e));
             ++launches;

@@ -308,7 +308,10 @@ cudaError_t launch_finalize_batch(int nb, int n, int M, const int64_t* blk_rows,
 cudaError_t launch_dense_step(int P, int prev, int64_t d, int64_t ld, const void* B, const void* xt_in,
                               int64_t dx, const float* own, const float* wprev, float* out, void* xt_out,
                               const uint32_t* vbits, double* tpart, const Params* prm, int mreal, uint32_t* err,
-                              cudaStream_t s);
+                              float* part, int* cnt, int smax, int grid, cudaStream_t s);
+// The dense step's stream-K schedule: persistent grid and piece slots per
+// 128-row tile (dense.cu).
+cudaError_t dense_schedule(int P, int64_t d, int sms, int* grid, int* smax);
 cudaError_t launch_dense_sign_split(int64_t d, int64_t dx, int P, int mreal, const uint32_t* vbits, void* xt,
                                     int grid, cudaStream_t s);
 cudaError_t launch_dense_gershgorin(int64_t d, int64_t ld, const void* B, double* partial, int grid, Params* prm,

@@ -2,12 +2,25 @@
 // (Sec. 2.2) when B is a dense d x d matrix stored in BF16, as a tensor-core
 // GEMM on sm_103a (tcgen05 + TMA + TMEM).
 //
-// Per CTA: 128 output rows (the MMA M), all P probes (the MMA N), the whole
-// row of B as K.  B tiles (128 rows x 64 columns, 128-byte swizzled) and the
-// matching W_j tiles are brought to shared memory by TMA through a ring of
-// stages; one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in
-// TMEM) and tcgen05.commit frees each stage; the four warps then read the
-// 128 x P accumulator from TMEM and apply the recurrence epilogue.
+// Work: 128-row tiles of the output (the MMA M) times all P probes (the MMA
+// N), each over K = d in blocks of 64 columns.  The (tile, K block) units are
+// split evenly over a persistent grid of as many CTAs as fit the GPU at once
+// (stream-K): each CTA takes a contiguous range of units, so one holds whole
+// tiles or pieces of up to a few.  (One CTA per tile left 48 of 152 SMs with
+// a single CTA at d = 32768, and one CTA's ring cannot keep an SM's share of
+// HBM busy: 88 % of the copy peak, 95 % when every SM held two.)
+//
+// Per CTA (192 threads): warp 4 brings each unit's B tile (128 rows x 64
+// columns, 128-byte swizzled) and W_j tiles to shared memory by TMA through
+// a ring of stages; warp 5 issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32
+// in TMEM) and tcgen05.commit frees each stage; warps 0-3 (the four TMEM lane
+// quarters) read a finished piece's accumulators and either apply the
+// recurrence epilogue (a whole tile) or store the piece's 128 x P partial sums
+// to the workspace.  The CTA that completes a tile's last piece (a per-tile
+// counter) adds the pieces in piece order and applies the epilogue, so no CTA
+// waits for another and the sums do not depend on which finishes last.  At
+// 32 and 64 probes TMEM holds two accumulator sets, so a piece's MMAs overlap
+// the previous piece's epilogue.
 //
 // W_j enters the MMA as an exact three-way BF16 split, w = hi + mid + lo
 // (hi = bf16(w), mid = bf16(w - hi), lo = bf16(w - hi - mid)): the MMA runs
@@ -16,8 +29,9 @@
 // stored probe-major ([part][probe][row]), the K-major layout of the MMA's B
 // operand, and double-buffered across steps.
 //
-// Every mbarrier wait is bounded; a wait that gives up sets *err, and the
-// CTA still frees its TMEM before returning.
+// Every mbarrier wait is bounded; a wait that gives up sets *err, the roles
+// wind down (their later waits give up too), and the CTA frees its TMEM once
+// the MMAs it issued have completed.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -29,10 +43,11 @@
 
 namespace cld {
 
-constexpr int kDRows = 128;     // MMA M: output rows per CTA
-constexpr int kDK = 64;         // K per stage: 64 BF16 = 128 bytes, one swizzle atom
+constexpr int kDRows = 128;     // MMA M: rows of a tile
+constexpr int kDK = 64;         // K per unit and stage: 64 BF16 = 128 bytes, one swizzle atom
 constexpr int kDSplit = 3;      // parts of the BF16 split of W
-constexpr int kDThreads = 128;  // 4 warps: TMEM lane quarters 0..3
+constexpr int kDEpi = 128;      // epilogue threads: warps 0-3, one TMEM lane (tile row) each
+constexpr int kDThreads = 192;  // + warp 4 (TMA producer) + warp 5 (MMA issuer)
 
 struct DenseArgs {
     int64_t d;
@@ -46,6 +61,9 @@ struct DenseArgs {
     const Params* prm;
     int mreal;
     uint32_t* err;
+    float* part;             // pieces' partial sums [ntiles][smax][128][P]
+    int* cnt;                // per tile: pieces finished in this step (0 between steps)
+    int smax;                // piece slots per tile
 };
 
 // ------------------------------------------------------------------ PTX helpers
@@ -114,70 +132,90 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 // ------------------------------------------------------------------ the step
 template <int P>
 struct DenseSmem {
-    // ring depth: 3 at P = 32 leaves room for two CTAs per SM (85 KB each),
-    // so one CTA's epilogue overlaps another's main loop (4 stages, 113 KB,
-    // measured 35 % slower); 4 at P = 64; 2 at 128
+    // ring depth: 3 at P = 32 leaves room for two CTAs per SM (4 stages,
+    // one CTA per SM, measured 35 % slower); 4 at P = 64; 2 at 128
     static constexpr int kStages = P == 32 ? 3 : P == 64 ? 4 : 2;
     static constexpr int kA = kDRows * kDK * 2;        // 16 KB
     static constexpr int kX = kDSplit * P * kDK * 2;   // 3 parts x P rows x 128 B
     static constexpr int kStage = kA + kX;
-    // the epilogue reuses the ring once every MMA has completed: the moment
-    // transpose [128][P+1] and, per warp, a 32 x 33 tile for its rows of
-    // w_j, w_{j-1} and w_{j+1} (coalesced loads and stores)
-    // The i-th K block a CTA takes goes to TMEM accumulator i mod kAcc; the
+    // The i-th K block of a piece goes to TMEM accumulator i mod kAcc; the
     // kAcc accumulators are added in FP32 (round to nearest) in the epilogue.
     // The tensor cores' accumulation rounds each addition in a way that does
     // not average out: the error grows with the additions into one accumulator
     // that follow a large term (it showed as a probe-independent moment bias,
     // logdet -1.15 instead of about -0.02 for a near-identity d = 32768
-    // matrix, -0.31 with 4 accumulators, -0.10 with 16).  So each CTA also
+    // matrix, -0.31 with 4 accumulators, -0.10 with 16).  So each tile also
     // takes its K blocks starting after its diagonal block, which comes last:
     // the large diagonal products meet few later additions.  (16 accumulators
     // need 512 TMEM columns, one CTA per SM: 35 % slower.)
     static constexpr int kAcc = 4;
-    static constexpr uint32_t kTmemCols = (uint32_t)(kAcc * P);  // 128, 256 or 512
-    static constexpr int kTr = kDRows * (P + 1) * 4;
-    static constexpr int kTile = 32 * 33 * 4;
-    static_assert(kTr + 2 * (kDThreads / 32) * kTile <= kStage * kStages, "epilogue buffers must fit the ring");
-    static constexpr int kBytes = kStage * kStages + 1024 /*align*/ + 256 /*barriers*/;
-    static_assert(kBytes <= 232448, "shared memory");
+    static constexpr int kBufs = P == 128 ? 1 : 2;  // accumulator sets (TMEM: 512 columns per SM)
+    static constexpr uint32_t kTmemCols = (uint32_t)(kBufs * kAcc * P);  // 256, 512, 512
+    static constexpr int kTr = kDRows * (P + 1) * 4;  // moment transpose [128][P+1]
+    static constexpr int kBars = 2 * kStages + 2 * kBufs + 1;
+    static constexpr int kBytes = kStage * kStages + kTr + 1024 /*align*/ + kBars * 8 + 32;
+    // resident CTAs per SM the grid is sized for: two at 32 probes (shared
+    // memory with the 1 KB per-CTA reservation, 2 x 256 TMEM columns, and the
+    // launch bounds' register cap), one otherwise
+    static constexpr int kPerSM = P == 32 ? 2 : 1;
+    static_assert(kPerSM * (kBytes + 1024) <= 233472, "shared memory of the CTAs an SM holds");
+    static_assert(kPerSM * kTmemCols <= 512, "TMEM columns of the CTAs an SM holds");
 };
 
+// Unit range of CTA c of G over U units, and the CTA holding unit x.
+__host__ __device__ inline int64_t dense_u0(int64_t U, int64_t c, int64_t G) { return U * c / G; }
+__host__ __device__ inline int64_t dense_owner(int64_t U, int64_t G, int64_t x) {
+    int64_t c = x * G / U;
+    while (c + 1 < G && dense_u0(U, c + 1, G) <= x) ++c;
+    while (c > 0 && dense_u0(U, c, G) > x) --c;
+    return c;
+}
+
 template <int P, int PREV>
-__global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
+__global__ void __launch_bounds__(kDThreads, DenseSmem<P>::kPerSM)
     dense_step_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmX,
                       const DenseArgs args) {
     using S = DenseSmem<P>;
-    constexpr int kDStages = S::kStages;
+    constexpr int NS = S::kStages;
+    constexpr int kAcc = S::kAcc, kBufs = S::kBufs;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t base = (raw + 1023u) & ~1023u;  // 1024-byte aligned ring (swizzle atoms)
     uint8_t* gbase = smem_raw + (base - raw);
-    const uint32_t bars = base + S::kStage * kDStages;  // full[S], empty[S], accum
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(gbase + (2 * kDStages + 1) * 8 + S::kStage * kDStages);
-    int* fail = reinterpret_cast<int*>(gbase + (2 * kDStages + 1) * 8 + 4 + S::kStage * kDStages);
-    // epilogue buffers in the ring (valid once the accumulator is complete)
-    float* tr = reinterpret_cast<float*>(gbase);  // [128][P+1]
-    float* tile_own = reinterpret_cast<float*>(gbase + S::kTr + (threadIdx.x >> 5) * 2 * S::kTile);  // [32][33]
-    float* tile_prev = tile_own + 32 * 33;
+    float* tr = reinterpret_cast<float*>(gbase + S::kStage * NS);  // [128][P+1]
+    const uint32_t bars = base + S::kStage * NS + S::kTr;
     auto full = [&](int s) { return bars + 8u * s; };
-    auto empty = [&](int s) { return bars + 8u * (kDStages + s); };
-    const uint32_t accum = bars + 8u * (2 * kDStages);
+    auto empty = [&](int s) { return bars + 8u * (NS + s); };
+    auto accf = [&](int b) { return bars + 8u * (2 * NS + b); };
+    auto acce = [&](int b) { return bars + 8u * (2 * NS + kBufs + b); };
+    const uint32_t done = bars + 8u * (2 * NS + 2 * kBufs);
+    uint8_t* misc = gbase + S::kStage * NS + S::kTr + S::kBars * 8;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(misc);
+    int* fail = reinterpret_cast<int*>(misc + 4);
+    int* lastflag = reinterpret_cast<int*>(misc + 8);
+    volatile int* votes = reinterpret_cast<volatile int*>(misc + 16);  // one per epilogue warp
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t row0 = (int64_t)blockIdx.x * kDRows;
-    const int nk = (int)((args.d + kDK - 1) / kDK);
+    const int64_t d = args.d;
+    const int64_t ntiles = (d + kDRows - 1) / kDRows;
+    const int nk = (int)((d + kDK - 1) / kDK);
+    const int64_t U = ntiles * nk, G = gridDim.x;
+    const int64_t u0 = dense_u0(U, blockIdx.x, G), u1 = dense_u0(U, blockIdx.x + 1, G);
 
     if (threadIdx.x == 0) {
         *fail = 0;
-        for (int s = 0; s < kDStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(full(s), 1);
             mbar_init(empty(s), 1);
         }
-        mbar_init(accum, 1);
+        for (int b = 0; b < kBufs; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), kDEpi / 32);
+        }
+        mbar_init(done, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {  // TMEM: P FP32 columns x 128 lanes
+    if (warp == 0) {  // TMEM: kBufs x kAcc x P FP32 columns x 128 lanes
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(S::kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -186,136 +224,259 @@ __global__ void __launch_bounds__(kDThreads, P == 32 ? 2 : 1)
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tmem_slot;
-    int issued = 0;  // producer: stages loaded
+    // the next step may be scheduled now: its CTAs take an SM's place as ours
+    // leave, and stream their first B tiles while ours finish
+    pdl_trigger();
 
-    if (warp == 0 && lane == 0) {
-        // producer: TMA into the ring; the i-th block taken is K block
-        // (kfirst + i) mod nk, so that the diagonal blocks (columns row0 ..
-        // row0 + 127) come last
-        const int kfirst = (int)(((row0 + kDRows) / kDK) % nk);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % kDStages;
-            if (kb >= kDStages && !mbar_wait(empty(s), ((kb / kDStages) - 1) & 1)) {
-                atomicExch(fail, 1);
-                break;
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer: unit u = tile u / nk, its (u mod nk)-th K block in the
+            // tile's order, (kfirst + i) mod nk, so that the diagonal blocks
+            // (columns row0 .. row0 + 127) come last
+            auto kblock = [&](int64_t u) {
+                const int64_t row0 = (u / nk) * kDRows;
+                const int kfirst = (int)(((row0 + kDRows) / kDK) % nk);
+                return (int)((kfirst + u % nk) % nk);
+            };
+            // the first ring fill's B tiles (written by no earlier kernel)
+            // before waiting for the predecessor; then their W_j tiles
+            const int64_t pre = u1 - u0 < NS ? u1 - u0 : NS;
+            for (int64_t g = 0; g < pre; ++g) {
+                const int s = (int)g;
+                mbar_expect_tx(full(s), S::kStage);
+                tma_load_2d(base + S::kStage * s, &tmA, full(s), kblock(u0 + g) * kDK, (int)(((u0 + g) / nk) * kDRows));
             }
-            mbar_expect_tx(full(s), S::kStage);
-            const uint32_t sa = base + S::kStage * s;
-            const int kx = (kfirst + kb) % nk;  // K block of this stage
-            tma_load_2d(sa, &tmA, full(s), kx * kDK, (int)row0);
-            for (int q = 0; q < kDSplit; ++q)
-                tma_load_2d(sa + S::kA + q * P * kDK * 2, &tmX, full(s), kx * kDK, q * P);
-            issued = kb + 1;
+            pdl_wait();
+            for (int64_t g = 0; g < pre; ++g) {
+                const uint32_t sa = base + S::kStage * (int)g;
+                for (int q = 0; q < kDSplit; ++q)
+                    tma_load_2d(sa + S::kA + q * P * kDK * 2, &tmX, full((int)g), kblock(u0 + g) * kDK, q * P);
+            }
+            int64_t issued = pre;
+            for (int64_t g = pre; u0 + g < u1; ++g) {
+                const int64_t u = u0 + g;
+                const int64_t row0 = (u / nk) * kDRows;
+                const int kx = kblock(u);
+                const int s = (int)(g % NS);
+                if (!mbar_wait(empty(s), (uint32_t)(((g / NS) - 1) & 1))) {
+                    atomicExch(fail, 1);
+                    break;
+                }
+                mbar_expect_tx(full(s), S::kStage);
+                const uint32_t sa = base + S::kStage * s;
+                tma_load_2d(sa, &tmA, full(s), kx * kDK, (int)row0);
+                for (int q = 0; q < kDSplit; ++q)
+                    tma_load_2d(sa + S::kA + q * P * kDK * 2, &tmX, full(s), kx * kDK, q * P);
+                issued = g + 1;
+            }
+            if (*fail)  // copies in flight land before the CTA exits (bounded)
+                for (int64_t g = issued > NS ? issued - NS : 0; g < issued; ++g)
+                    mbar_wait(full((int)(g % NS)), (uint32_t)((g / NS) & 1));
         }
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer
-        constexpr uint32_t idesc = idesc_bf16(kDRows, P);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % kDStages;
-            if (!mbar_wait(full(s), (kb / kDStages) & 1)) {
+    } else if (warp == 5) {
+        if (lane == 0) {
+            // MMA issuer: one piece (the CTA's units of one tile) per
+            // accumulator set
+            constexpr uint32_t idesc = idesc_bf16(kDRows, P);
+            int64_t g = 0;
+            int piece = 0;
+            bool ok = true;
+            for (int64_t ps = u0; ps < u1 && ok; ++piece) {
+                const int64_t t = ps / nk;
+                const int64_t pe = (t + 1) * nk < u1 ? (t + 1) * nk : u1;
+                const int b = piece % kBufs, use = piece / kBufs;
+                if (use >= 1 && !mbar_wait(acce(b), (uint32_t)((use - 1) & 1))) {
+                    atomicExch(fail, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                for (int64_t u = ps; u < pe; ++u, ++g) {
+                    const int s = (int)(g % NS);
+                    if (!mbar_wait(full(s), (uint32_t)((g / NS) & 1))) {
+                        atomicExch(fail, 1);
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sa = base + S::kStage * s;
+                    const int i = (int)(u - ps);  // index within the piece
+                    const uint32_t dcol = tmem + (uint32_t)((b * kAcc + i % kAcc) * P);
+#pragma unroll
+                    for (int kk = 0; kk < kDK / 16; ++kk) {
+                        const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+#pragma unroll
+                        for (int q = 0; q < kDSplit; ++q) {
+                            const uint64_t bd = smem_desc_sw128(sa + S::kA + q * P * kDK * 2 + kk * 32);
+                            // the first MMA of an accumulator in a piece overwrites
+                            umma_bf16(dcol, ad, bd, idesc, (i >= kAcc || kk != 0 || q != 0) ? 1u : 0u);
+                        }
+                    }
+                    umma_commit(empty(s));
+                }
+                if (!ok) break;
+                umma_commit(accf(b));  // arrives once the piece's MMAs have completed
+                ps = pe;
+            }
+            umma_commit(done);  // every MMA issued above has completed
+        }
+    } else {
+        // epilogue warps: thread = TMEM lane = row of the tile; they read
+        // w_j, w_{j-1} and the signs and write w_{j+1}, its split, the
+        // partial sums and the counters: after the predecessor
+        pdl_wait();
+        constexpr int NW = P <= 32 ? 1 : P / 32;
+        const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
+        const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
+        const uint32_t lanebase = tmem + ((uint32_t)(warp * 32) << 16);
+        int piece = 0;
+        for (int64_t ps = u0; ps < u1; ++piece) {
+            const int64_t t = ps / nk;
+            const int64_t pe = (t + 1) * nk < u1 ? (t + 1) * nk : u1;
+            const int b = piece % kBufs, use = piece / kBufs;
+            const int nacc = (int)(pe - ps < kAcc ? pe - ps : kAcc);  // accumulators written
+            // the four warps decide together (a warp leaving alone would
+            // strand the others at the named barriers below)
+            const bool okw = __all_sync(0xffffffffu, mbar_wait(accf(b), (uint32_t)(use & 1)));
+            if (lane == 0) votes[warp] = okw ? 1 : 0;
+            asm volatile("bar.sync 1, %0;" ::"r"(kDEpi) : "memory");
+            const bool ok = votes[0] && votes[1] && votes[2] && votes[3];
+            asm volatile("bar.sync 1, %0;" ::"r"(kDEpi) : "memory");
+            if (!ok) {
                 atomicExch(fail, 1);
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t sa = base + S::kStage * s;
+            const int64_t row = t * kDRows + threadIdx.x;
+            const bool live = row < d;
+            const bool whole = ps == t * nk && pe == (t + 1) * nk;
+            // the recurrence epilogue of columns c0 .. c0 + 31 from the tile
+            // sums acc (w_{j+1} rows, its split, the moment terms)
+            auto finish = [&](int c0, const float (&acc)[32]) {
+                if (live) {
+                    const uint32_t word = __ldg(args.vbits + row * NW + c0 / 32);
 #pragma unroll
-            for (int kk = 0; kk < kDK / 16; ++kk) {
-                const uint64_t ad = smem_desc_sw128(sa + kk * 32);
+                    for (int qg = 0; qg < 32; qg += 4) {
+                        float4 o4 = make_float4(0.f, 0.f, 0.f, 0.f), p4 = o4;
+                        if (PREV != 0) o4 = __ldg(reinterpret_cast<const float4*>(args.own + row * P + c0 + qg));
+                        if (PREV == 2) p4 = __ldg(reinterpret_cast<const float4*>(args.wprev + row * P + c0 + qg));
+                        const float ov[4] = {o4.x, o4.y, o4.z, o4.w}, pvv[4] = {p4.x, p4.y, p4.z, p4.w};
+                        float wv[4];
 #pragma unroll
-                for (int q = 0; q < kDSplit; ++q) {
-                    const uint64_t bd = smem_desc_sw128(sa + S::kA + q * P * kDK * 2 + kk * 32);
-                    // accumulator kb mod kAcc; its first MMA overwrites
-                    umma_bf16(tmem + (uint32_t)((kb % S::kAcc) * P), ad, bd, idesc,
-                              (kb >= S::kAcc || kk != 0 || q != 0) ? 1u : 0u);
+                        for (int e = 0; e < 4; ++e) {
+                            const int q = qg + e, p = c0 + q;
+                            const float vm = p < args.mreal ? 1.f : 0.f;
+                            const float v = vm * __uint_as_float(0x3f800000u | (((word >> q) & 1u) << 31));
+                            const float own = PREV == 0 ? v : ov[e];
+                            const float y = fmaf(scale, acc[q], -shift * own) + fmaf(scale_lo, acc[q], -shift_lo * own);
+                            const float w = PREV == 0 ? y : fmaf(2.f, y, -(PREV == 1 ? v : pvv[e]));
+                            wv[e] = w;
+                            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+                            const float r1 = w - __bfloat162float(hi);
+                            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+                            const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+                            args.xt_out[(0 * P + p) * args.dx + row] = hi;
+                            args.xt_out[(1 * P + p) * args.dx + row] = mid;
+                            args.xt_out[(2 * P + p) * args.dx + row] = lo;
+                            tr[threadIdx.x * (P + 1) + p] = v * w;
+                        }
+                        *reinterpret_cast<float4*>(args.out + row * P + c0 + qg) = make_float4(wv[0], wv[1], wv[2], wv[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) tr[threadIdx.x * (P + 1) + c0 + q] = 0.f;
                 }
-            }
-            umma_commit(empty(s));
-        }
-        umma_commit(accum);  // arrives once every MMA issued above has completed
-    }
-    // epilogue: row = row0 + threadIdx.x (TMEM lane = thread), P columns
-    const bool got = mbar_wait(accum, 0);
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const bool good = got && *fail == 0;
-    const int64_t row = row0 + threadIdx.x;
-    const bool live = row < args.d;
-    if (good) {
-        const float scale = args.prm->scale_hi, scale_lo = args.prm->scale_lo;
-        const float shift = args.prm->shift_hi, shift_lo = args.prm->shift_lo;
-        constexpr int NW = P <= 32 ? 1 : P / 32;
-        // this warp's rows rw .. rw + nr - 1 (thread lane holds row rw + lane)
-        const int64_t rw = row0 + warp * 32;
-        const int nr = (int)(args.d - rw < 32 ? (args.d - rw > 0 ? args.d - rw : 0) : 32);
+            };
+            // this piece's sums of columns c0 .. c0 + 31: the written
+            // accumulators added in a fixed order
+            auto piece_sums = [&](int c0, float (&acc)[32]) {
+                tmem_ld32(lanebase + (uint32_t)(b * kAcc * P + c0), acc);
 #pragma unroll 1
-        for (int c0 = 0; c0 < P; c0 += 32) {
-            float acc[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, acc);
-            // the other accumulators, added in a fixed order (those that never
-            // received an MMA, when nk < kAcc, are skipped)
-#pragma unroll 1
-            for (int a = 1; a < S::kAcc && a < nk; ++a) {
-                float part[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * P + c0), part);
+                for (int a = 1; a < nacc; ++a) {
+                    float part[32];
+                    tmem_ld32(lanebase + (uint32_t)((b * kAcc + a) * P + c0), part);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) acc[q] += part[q];
-            }
-            // columns c0 .. c0 + 31 of w_j and w_{j-1} for the warp's rows, one
-            // 128-byte row at a time
-            for (int r = 0; r < nr; ++r) {
-                if (PREV != 0) tile_own[r * 33 + lane] = __ldg(args.own + (rw + r) * P + c0 + lane);
-                if (PREV == 2) tile_prev[r * 33 + lane] = __ldg(args.wprev + (rw + r) * P + c0 + lane);
-            }
-            __syncwarp();
-            if (live) {
-                const uint32_t word = __ldg(args.vbits + row * NW + c0 / 32);
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    const int p = c0 + q;
-                    const float vm = p < args.mreal ? 1.f : 0.f;
-                    const float v = vm * __uint_as_float(0x3f800000u | (((word >> q) & 1u) << 31));
-                    const float own = PREV == 0 ? v : tile_own[lane * 33 + q];
-                    float y = fmaf(scale, acc[q], -shift * own) + fmaf(scale_lo, acc[q], -shift_lo * own);
-                    float w;
-                    if (PREV == 0) w = y;
-                    else w = fmaf(2.f, y, -(PREV == 1 ? v : tile_prev[lane * 33 + q]));
-                    tile_own[lane * 33 + q] = w;  // w_{j+1}, stored below by rows
-                    const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-                    const float r1 = w - __bfloat162float(hi);
-                    const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-                    const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-                    args.xt_out[(0 * P + p) * args.dx + row] = hi;
-                    args.xt_out[(1 * P + p) * args.dx + row] = mid;
-                    args.xt_out[(2 * P + p) * args.dx + row] = lo;
-                    tr[threadIdx.x * (P + 1) + p] = v * w;
+                    for (int q = 0; q < 32; ++q) acc[q] += part[q];
                 }
+            };
+            auto release = [&]() {  // TMEM set b read: the MMA issuer may refill it
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce(b));
+            };
+            bool fin = whole;
+            if (whole) {
+#pragma unroll 1
+                for (int c0 = 0; c0 < P; c0 += 32) {
+                    float acc[32];
+                    piece_sums(c0, acc);
+                    finish(c0, acc);
+                }
+                release();
             } else {
+                // a piece of a shared tile: its partial sums to slot
+                // (this CTA - the tile's first CTA), then the tile's counter
+                const int64_t cfirst = dense_owner(U, G, t * nk);
+                const int np = (int)(dense_owner(U, G, (t + 1) * nk - 1) - cfirst + 1);
+                const int slot = (int)(blockIdx.x - cfirst);
+                float* mine = args.part + ((t * args.smax + slot) * kDRows + threadIdx.x) * P;
+#pragma unroll 1
+                for (int c0 = 0; c0 < P; c0 += 32) {
+                    float acc[32];
+                    piece_sums(c0, acc);
 #pragma unroll
-                for (int q = 0; q < 32; ++q) tr[threadIdx.x * (P + 1) + c0 + q] = 0.f;
+                    for (int q = 0; q < 32; q += 4)
+                        *reinterpret_cast<float4*>(mine + c0 + q) = make_float4(acc[q], acc[q + 1], acc[q + 2], acc[q + 3]);
+                }
+                release();
+                __threadfence();
+                asm volatile("bar.sync 1, %0;" ::"r"(kDEpi) : "memory");
+                if (threadIdx.x == 0) *lastflag = atomicAdd(args.cnt + t, 1) == np - 1 ? 1 : 0;
+                asm volatile("bar.sync 1, %0;" ::"r"(kDEpi) : "memory");
+                fin = *lastflag != 0;
+                if (fin) {
+                    // the tile's last piece: all pieces, added in slot order
+                    __threadfence();
+                    if (threadIdx.x == 0) args.cnt[t] = 0;  // ready for the next step
+                    const float* first = args.part + ((t * args.smax) * kDRows + threadIdx.x) * P;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < P; c0 += 32) {
+                        float acc[32];
+#pragma unroll
+                        for (int q = 0; q < 32; q += 4) {
+                            const float4 a = __ldcg(reinterpret_cast<const float4*>(first + c0 + q));
+                            acc[q] = a.x; acc[q + 1] = a.y; acc[q + 2] = a.z; acc[q + 3] = a.w;
+                        }
+#pragma unroll 1
+                        for (int k = 1; k < np; ++k) {
+                            const float* src = first + (int64_t)k * kDRows * P;
+#pragma unroll
+                            for (int q = 0; q < 32; q += 4) {
+                                const float4 a = __ldcg(reinterpret_cast<const float4*>(src + c0 + q));
+                                acc[q] += a.x; acc[q + 1] += a.y; acc[q + 2] += a.z; acc[q + 3] += a.w;
+                            }
+                        }
+                        finish(c0, acc);
+                    }
+                }
             }
-            __syncwarp();
-            for (int r = 0; r < nr; ++r) args.out[(rw + r) * P + c0 + lane] = tile_own[r * 33 + lane];
-            __syncwarp();
-        }
-    } else {
-        if (threadIdx.x == 0) atomicOr(args.err, 1u);
-        // a wait gave up: let copies and MMAs already issued finish (bounded)
-        if (warp == 0 && lane == 0)
-            for (int kb = issued > kDStages ? issued - kDStages : 0; kb < issued; ++kb)
-                mbar_wait(full(kb % kDStages), (kb / kDStages) & 1);
-        if (!got) mbar_wait(accum, 0);
-    }
-    __syncthreads();
-    if (good) {
-        for (int p = threadIdx.x; p < P; p += kDThreads) {
-            double s = 0.0;
-            for (int t = 0; t < kDRows; ++t) s += (double)tr[t * (P + 1) + p];
-            args.tpart[(int64_t)blockIdx.x * P + p] = s;
+            if (fin) {
+                // the tile's moment terms summed over its rows in order
+                asm volatile("bar.sync 1, %0;" ::"r"(kDEpi) : "memory");
+                for (int p = threadIdx.x; p < P; p += kDEpi) {
+                    double s = 0.0;
+                    for (int r = 0; r < kDRows; ++r) s += (double)tr[r * (P + 1) + p];
+                    args.tpart[t * P + p] = s;
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(kDEpi) : "memory");
+            }
+            ps = pe;
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
+    if (threadIdx.x == 0 && *fail) atomicOr(args.err, 1u);
+    // free TMEM once the MMAs issued have completed (bounded)
     if (warp == 0) {
+        mbar_wait(done, 0);
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(S::kTmemCols));
     }
@@ -423,33 +584,70 @@ static bool make_map(CUtensorMap* m, const void* ptr, int64_t inner, int64_t out
     return r == CUDA_SUCCESS;
 }
 
-int dense_smem_bytes(int P) {
-    switch (P) {
-        case 32: return DenseSmem<32>::kBytes;
-        case 64: return DenseSmem<64>::kBytes;
-        case 128: return DenseSmem<128>::kBytes;
-        default: return 0;
+// Opts the dense kernel into its shared memory and the largest carveout
+// (two CTAs need 210 KB at P = 32; the rest of a step needs little L1), once.
+template <int P, int PREV>
+static cudaError_t dense_opt_in() {
+    static bool done = false;
+    if (done) return cudaSuccess;
+    const int smem = DenseSmem<P>::kBytes;
+    cudaError_t e = cudaFuncSetAttribute(dense_step_kernel<P, PREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(dense_step_kernel<P, PREV>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+// The stream-K schedule of a step: a persistent grid of as many CTAs as fit
+// the GPU at once (at most one per unit), and the most pieces any tile is
+// cut into (the slots of the partial-sum buffer).
+cudaError_t dense_schedule(int P, int64_t d, int sms, int* grid, int* smax) {
+    const int per_sm = P == 32 ? DenseSmem<32>::kPerSM : P == 64 ? DenseSmem<64>::kPerSM
+                     : P == 128 ? DenseSmem<128>::kPerSM : 0;
+    if (per_sm <= 0) return cudaErrorInvalidValue;
+    const int64_t ntiles = (d + kDRows - 1) / kDRows, nk = (d + kDK - 1) / kDK, U = ntiles * nk;
+    int64_t G = (int64_t)per_sm * (sms > 0 ? sms : 1);
+    if (G > U) G = U;
+    if (G < 1) G = 1;
+    int64_t most = 1;
+    for (int64_t t = 0; t < ntiles; ++t) {
+        const int64_t np = dense_owner(U, G, (t + 1) * nk - 1) - dense_owner(U, G, t * nk) + 1;
+        most = np > most ? np : most;
     }
+    *grid = (int)G;
+    *smax = (int)most;
+    return cudaSuccess;
 }
 
 template <int P, int PREV>
 static cudaError_t launch_dense_t(const CUtensorMap& a, const CUtensorMap& x, int grid, cudaStream_t s,
                                   const DenseArgs& args) {
-    const int smem = DenseSmem<P>::kBytes;
-    cudaError_t e = cudaFuncSetAttribute(dense_step_kernel<P, PREV>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = dense_opt_in<P, PREV>();
     if (e != cudaSuccess) return e;
-    dense_step_kernel<P, PREV><<<grid, kDThreads, smem, s>>>(a, x, args);
-    return cudaGetLastError();
+    // programmatic stream serialization (see pdl_wait): a step's CTAs start
+    // as the previous step's leave
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid, 1, 1);
+    cfg.blockDim = dim3((unsigned)kDThreads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)DenseSmem<P>::kBytes;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, dense_step_kernel<P, PREV>, a, x, args);
 }
 
 // Host entry used by cld_api.cu.  B: d x d BF16 with leading dimension ld
 // (elements); xt_in: the split of w_j ([3][P][dx]); prev: 0 first step,
-// 1 second, 2 general.  Returns cudaErrorNotSupported when the tensor map
-// cannot be encoded.
+// 1 second, 2 general; grid, part (ntiles x smax x 128 x P floats) and cnt
+// (ntiles ints, zero before the first step) from dense_schedule.  Returns
+// cudaErrorNotSupported when the tensor map cannot be encoded.
 cudaError_t launch_dense_step(int P, int prev, int64_t d, int64_t ld, const void* B, const void* xt_in,
                               int64_t dx, const float* own, const float* wprev, float* out, void* xt_out,
                               const uint32_t* vbits, double* tpart, const Params* prm, int mreal, uint32_t* err,
-                              cudaStream_t s) {
+                              float* part, int* cnt, int smax, int grid, cudaStream_t s) {
     CUtensorMap ma, mx;
     if (!make_map(&ma, B, d, d, ld, kDRows)) return cudaErrorNotSupported;
     // inner extent d: columns k >= d of the split (never written) read as 0
@@ -466,7 +664,9 @@ cudaError_t launch_dense_step(int P, int prev, int64_t d, int64_t ld, const void
     a.prm = prm;
     a.mreal = mreal;
     a.err = err;
-    const int grid = (int)((d + kDRows - 1) / kDRows);
+    a.part = part;
+    a.cnt = cnt;
+    a.smax = smax;
 #define CLD_DENSE_CASE(PP)                                                   \
     case PP:                                                                 \
         return prev == 0 ? launch_dense_t<PP, 0>(ma, mx, grid, s, a)         \
