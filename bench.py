@@ -922,23 +922,32 @@ def dense_leg(args, torch):
             "kernel": "dense_step_kernel (tcgen05.mma kind::f16, TMA, TMEM)"}
 
 
+def step_sources_sha256(csrc):
+    """sha256 of the step kernels' device code, value loads and grid sizing:
+    their headers, and the argument block (struct StepArgs) of the shared
+    internal header, whose other declarations do not reach these kernels."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("step_kernel.cuh", "step_wide.cuh", "step_staged.cuh", "step_window.cuh", "async_copy.cuh",
+                 "step_launch.cuh"):
+        h.update(open(os.path.join(csrc, name), "rb").read())
+    internal = open(os.path.join(csrc, "cld_internal.cuh"), "rb").read()
+    i = internal.index(b"struct StepArgs {")
+    h.update(internal[i:internal.index(b"};", i) + 2])
+    return h.hexdigest()
+
+
 def profiled_traffic(args, B, variant):
     """DRAM bytes (read + write) per general-step launch of inner-loop variant
     ``variant`` from the committed ncu summary of this workload, if the step
     kernel's source is the one it was captured with."""
-    import hashlib
-
     path = os.path.join(ROOT, "profiles", "step_kernel_config2_traffic.md")
     csrc = os.path.join(ROOT, "paper_1503_06394_gb300", "csrc")
     if args.config != 2 or args.d or args.dtype != "f32" or not os.path.exists(path):
         return None
     text = open(path).read()
-    h = hashlib.sha256()
-    # the device code of every variant, its value loads and its grid sizing
-    for name in ("step_kernel.cuh", "step_wide.cuh", "step_staged.cuh", "step_window.cuh", "async_copy.cuh",
-                 "cld_internal.cuh", "step_launch.cuh"):
-        h.update(open(os.path.join(csrc, name), "rb").read())
-    want = h.hexdigest()
+    want = step_sources_sha256(csrc)
     vals = dict(line.split(":", 1) for line in text.splitlines() if ":" in line and line[:1].isalpha())
     if vals.get("step_kernels_sha256", "").strip() != want:
         return None
