@@ -50,8 +50,8 @@ def run_dense(b16, d, a, b, n, M, seed):
     return r
 
 
-def check_dense(d, M, n, seed=0, density=1.0):
-    b16, A = dense_spd_bf16(d, 100 + d, density)
+def check_dense(d, M, n, seed=0, density=1.0, margin=1.0):
+    b16, A = dense_spd_bf16(d, 100 + d, density, margin)
     rowptr, col, val = csr_of(A)
     lo, hi = oracle.gershgorin(rowptr, col, val)
     if not hi - lo > 1e-9 * hi:  # one-point spectrum (d = 1): widen
@@ -141,3 +141,43 @@ def test_dense_multi_tile_sampled(torch):
         d, (dt / tol).max(), ["%.2e" % x for x in rel], dt[1]))
     assert np.all(dt <= tol), (dt / tol).max()
     assert max(rel) <= 1e-5
+
+
+@pytest.mark.parametrize("M", [64, 128])
+def test_dense_pieces_reuse_tmem(torch, M):
+    """d = 2000 at 64 and 128 probes (one CTA per SM): 16 row tiles of 32
+    K blocks over 152 stream-K CTAs, so CTAs hold two pieces of adjacent
+    tiles and the accumulator sets are reused (one set at 128 probes: the
+    second piece's MMAs wait for the first piece's epilogue).  Every moment
+    against the oracle on the same BF16 values."""
+    check_dense(2000, M, 6, seed=M, margin=1.1)
+
+
+def test_dense_more_tiles_than_ctas(torch):
+    """d = 40960: 320 row tiles of 640 K blocks over 304 stream-K CTAs, so some
+    CTAs hold the end of one tile, a whole tile and the start of a third, and
+    each accumulator set serves several pieces.  The Kac-Murdock-Szego matrix
+    0.5^|i-k| (exact in BF16) against its closed-form logdet within 4
+    standard errors, and two estimates bit-identical (a tile's pieces are added
+    in piece order, whichever CTA finishes it)."""
+    from paper_1503_06394_gb300 import DenseLogdet
+
+    d, n, M, rho = 40960, 30, 32, 0.5
+    free, _ = torch.cuda.mem_get_info()
+    if free < 8e9:
+        pytest.skip("needs about 8 GB of free device memory")
+    Ab = torch.empty((d, d), dtype=torch.bfloat16, device="cuda")
+    cols = torch.arange(d, device="cuda", dtype=torch.float32)
+    for r0 in range(0, d, 2048):
+        rows = torch.arange(r0, min(d, r0 + 2048), device="cuda", dtype=torch.float32)
+        Ab[r0:r0 + rows.numel()] = torch.pow(rho, (rows[:, None] - cols[None, :]).abs()).to(torch.bfloat16)
+    m = DenseLogdet(Ab, d)
+    m.set_interval((1 - rho) / (1 + rho), (1 + rho) / (1 - rho))
+    r1 = m.estimate(n, M, 3, moments=True)
+    r2 = m.estimate(n, M, 3, moments=True)
+    m.close()
+    del Ab
+    torch.cuda.empty_cache()
+    exact = oracle.kms_logdet(d, rho)
+    assert abs(r1["logdet"] - exact) <= 4 * r1["stderr"], (r1["logdet"], exact, r1["stderr"])
+    assert r1["logdet"] == r2["logdet"] and np.array_equal(r1["t"], r2["t"])
