@@ -74,14 +74,16 @@ __host__ __device__ constexpr int staged_up16(int x) { return (x + 15) / 16 * 16
 // Ring shape from a stage's size at a given entry capacity (`stage_of(capr)`:
 // bytes of one stage holding capr stored entries a row) and the static shared
 // memory at a given stage count (`static_of(ns)`, an upper bound): 16 entries a
-// row if two stages fit the CTA's share, else 12 if two stages fit, else 16
-// (the CTA then takes more than its share and the SM holds fewer CTAs or less
-// L1); then as many stages (2 to 4) as fit.  Tiles with more entries than the
-// capacity read their indices and values from global memory.
+// row if three stages fit the CTA's share, or if two do and 12 entries would
+// not make room for a third; else 12 if two stages fit; else 16 (the CTA then
+// takes more than its share and the SM holds fewer CTAs or less L1); then as
+// many stages (2 to 4) as fit.  (The third stage measured 2 % faster on the
+// five-point grid at 64 probes, whose rows hold 5 entries.)  Tiles with more
+// entries than the capacity read their indices and values from global memory.
 template <class L, class C>
 struct StagedRing {
     static constexpr bool fits(int capr, int ns) { return ns * L::stage_of(capr) + L::static_of(ns) <= C::cta_bytes; }
-    static constexpr int capr = fits(16, 2) ? 16 : fits(12, 2) ? 12 : 16;
+    static constexpr int capr = fits(16, 3) || (fits(16, 2) && !fits(12, 3)) ? 16 : fits(12, 2) ? 12 : 16;
     static constexpr int ns = fits(capr, 4) ? 4 : fits(capr, 3) ? 3 : 2;
 };
 
