@@ -125,8 +125,8 @@ CLD_API cld_status cld_workspace_size(cld_handle h, int n, int M, int with_grad,
 CLD_API cld_status cld_set_workspace(cld_handle h, void* dev_ptr, size_t bytes);
 
 /* Sets the spectral interval [a, b] that must contain the spectrum of B
- * (CLD_SPD) or of C^T C (CLD_GENERAL), Sec. 3 ("loose lower and upper bounds
- * suffice").  Errors: CLD_ERR_INTERVAL if !(0 < a < b) or not finite. */
+ * (CLD_SPD) or of C^T C (CLD_GENERAL); by Sec. 3 the bounds may be loose
+ * (a wider interval costs accuracy at a given degree, not correctness).  Errors: CLD_ERR_INTERVAL if !(0 < a < b) or not finite. */
 CLD_API cld_status cld_set_interval(cld_handle h, double a, double b);
 
 /* Computes an interval on the device and stores it on the handle (Sec. 3.2).
@@ -374,7 +374,9 @@ CLD_API cld_status cld_last_timing(cld_handle h, float* step_ms, int* step_launc
 
 /* Kernel configuration of the recurrence step, for reports (no paper
  * counterpart): probe panel width
- * (padded M), lanes per row, CTAs per launch, threads per CTA. */
+ * (padded M), lanes per row, CTAs per launch, threads per CTA (dense
+ * handles: the stream-K step's persistent grid, one epilogue thread per row
+ * of a tile). */
 CLD_API cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row, int* ctas,
                              int* threads);
 

@@ -1454,6 +1454,14 @@ cld_status cld_launch_config(cld_handle h, int M, int* panel, int* lanes_per_row
     if (M < 1) return fail(CLD_ERR_INVALID, "M >= 1");
     const Layout L = make_layout(h, 1, M, 0);
     if (panel) *panel = L.panel;
+    if (h->dense) {
+        // the stream-K tensor-core step: one thread (TMEM lane) per row of a
+        // tile in the epilogue, a persistent grid
+        if (lanes_per_row) *lanes_per_row = 1;
+        if (ctas) *ctas = L.dgrid;
+        if (threads) *threads = dense_threads_per_cta();
+        return CLD_OK;
+    }
     // 4 probes per lane; 8 with the wide lanes (variant 5, panels of 8 or more)
     const bool wide = h->impl >= 5 && h->nb == 0 && L.panel >= 8;
     if (lanes_per_row) *lanes_per_row = wide ? L.panel / 8 : L.panel / 4;

@@ -312,6 +312,7 @@ cudaError_t launch_dense_step(int P, int prev, int64_t d, int64_t ld, const void
 // The dense step's stream-K schedule: persistent grid and piece slots per
 // 128-row tile (dense.cu).
 cudaError_t dense_schedule(int P, int64_t d, int sms, int* grid, int* smax);
+int dense_threads_per_cta();
 cudaError_t launch_dense_sign_split(int64_t d, int64_t dx, int P, int mreal, const uint32_t* vbits, void* xt,
                                     int grid, cudaStream_t s);
 cudaError_t launch_dense_gershgorin(int64_t d, int64_t ld, const void* B, double* partial, int grid, Params* prm,

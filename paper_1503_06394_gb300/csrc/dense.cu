@@ -598,6 +598,8 @@ static cudaError_t dense_opt_in() {
     return e;
 }
 
+int dense_threads_per_cta() { return kDThreads; }
+
 // The stream-K schedule of a step: a persistent grid of as many CTAs as fit
 // the GPU at once (at most one per unit), and the most pieces any tile is
 // cut into (the slots of the partial-sum buffer).

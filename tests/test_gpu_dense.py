@@ -69,6 +69,23 @@ def test_dense_one_tile_one_step(torch):
     check_dense(128, 32, 1)
 
 
+def test_dense_launch_config_reports_stream_k(torch):
+    """cld_launch_config on a dense handle reports the stream-K step's launch:
+    a persistent grid of at most two CTAs per SM at 32 probes (one at 64),
+    never more CTAs than (tile, K block) units, 192 threads each.  d = 1000:
+    8 row tiles x 16 K blocks = 128 units, so 128 CTAs; d = 2048: 512 units,
+    so two (one) CTAs per SM."""
+    from paper_1503_06394_gb300 import DenseLogdet
+
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    for d, M, want in ((1000, 32, 128), (2048, 32, min(512, 2 * sms)), (2048, 64, min(512, sms))):
+        b16, _ = dense_spd_bf16(d, 7)
+        m = DenseLogdet(b16, d)
+        got = m.launch_config(M)
+        m.close()
+        assert tuple(got) == (32 if M <= 32 else 64, 1, want, 192), (d, M, got)
+
+
 @pytest.mark.parametrize("d", [1, 8, 64, 100, 130, 200, 1000])
 @pytest.mark.parametrize("M", [1, 32, 33, 64, 128, 130])
 def test_dense_shapes(torch, d, M):
